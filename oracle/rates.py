@@ -1,0 +1,54 @@
+"""Rate coefficients for hydrogen-only gas (oracle; test infrastructure only).
+
+Sec. "Physical Model": G, Lambda, alpha_ij and Gamma^ph are functions of T, E and
+the ionisation state, with formulas the paper cites but does not print.  Readings
+used (identical in the CUDA library, written there independently):
+
+* alpha(T): the constant alpha_B = 2.59e-13 cm^3/s quoted in the verification
+  section (mode "const"), or the Hui & Gnedin (1997) case-B fit (mode "hg97").
+* Photo-heating per unit volume: n_HI c E (sigma_E - h nu_0 sigma_G)   (grey
+  averages from ``spectrum``).
+* Cooling per unit volume: case-B recombination cooling (Hui & Gnedin 1997),
+  collisional excitation of HI and bremsstrahlung (Cen 1992), Compton cooling
+  off the CMB (4 k_B sigma_T a_rad T_cmb^4 (T - T_cmb) n_e / (m_e c)).
+  Collisional ionisation is not included.
+
+Pins: alpha_hg97(1e4 K) reproduces the paper's 2.59e-13 to 0.1 %.  The cooling
+functions and the shape of alpha_hg97 away from 1e4 K are parity unpinned
+(no printed value in the paper; implementation-against-implementation only).
+
+All functions accept complex arguments (the oracle Jacobian uses complex steps).
+"""
+import numpy as np
+
+from . import constants as K
+
+T_HI = 157807.0   # K, hydrogen ionisation temperature used by the Hui & Gnedin fits
+T_FLOOR = 1.0     # K, rates are evaluated at max(T, T_FLOOR)
+
+
+def _cmax(x, c):
+    """max(x, c) compared on real parts (complex-step safe)."""
+    return np.where(np.real(x) >= c, x, c)
+
+
+def alpha_B(T, mode):
+    """Case-B recombination coefficient [cm^3/s]."""
+    if mode == "const":
+        return K.ALPHA_B_PAPER + 0.0 * T
+    T = _cmax(T, T_FLOOR)
+    lam = 2.0 * T_HI / T
+    return 2.753e-14 * lam**1.5 / (1.0 + (lam / 2.740) ** 0.407) ** 2.242
+
+
+def cooling_rate(T, n_e, n_HI, n_HII, a):
+    """Total cooling Lambda per unit proper volume [erg cm^-3 s^-1] (proper densities)."""
+    T = _cmax(T, T_FLOOR)
+    lam = 2.0 * T_HI / T
+    rec = 3.435e-30 * T * lam**1.970 / (1.0 + (lam / 2.250) ** 0.376) ** 3.720 * n_e * n_HII
+    ce = 7.5e-19 * np.exp(-118348.0 / T) / (1.0 + np.sqrt(T / 1e5)) * n_e * n_HI
+    gff = 1.1 + 0.34 * np.exp(-((5.5 - np.log10(T)) ** 2) / 3.0)
+    ff = 1.42e-27 * gff * np.sqrt(T) * n_e * n_HII
+    T_cmb = K.T_CMB0 / a
+    comp = 4.0 * K.K_BOLTZ * K.SIGMA_T * K.A_RAD * T_cmb**4 / (K.M_E * K.C_LIGHT) * (T - T_cmb) * n_e
+    return rec + ce + ff + comp
