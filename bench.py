@@ -1,0 +1,352 @@
+"""Benchmark: cell-steps/s of the implicit FLD + ionisation + heating step.
+
+Workload: the reionization-like field at 256^3 (periodic 14.4 Mpc comoving box at z = 9,
+log-normal density, 2000 density-peak sources, Gaussian velocities; see ``workloads``),
+one implicit step (v) per timed step: setup, globalised Newton with nonlinear
+elimination of the local block, Schur-reduced FP64 CG with a multigrid preconditioner,
+and the gas-energy hand-over e_h += e_c.  ``value`` is the mixed path (FP32 multigrid
+inside FP64 Newton/CG); the all-FP64 path is timed the same way and reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--size 256]
+Under torchrun each rank runs an independent replica on its own GPU ("replicas only":
+the step has no cross-GPU exchange on one GPU per problem).  ``--impl reference`` times
+the FP64 CPU oracle on host cores instead (bounded sub-block samples of the workload).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-steps/s of implicit FLD+chem solve, 256^3, mixed vs FP64; V-cycle HBM GB/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=4)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--size", type=int, default=256)
+    p.add_argument("--newton-tol", type=float, default=1e-6)
+    p.add_argument("--lin-rtol", type=float, default=1e-3)
+    p.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison run")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return p.parse_args()
+
+
+def workload(n):
+    import workloads as W
+    return W.reionization_field(n=n, nsrc=2000 if n >= 128 else max(2, 2000 * n**3 // 256**3),
+                                box_mpc=14.4 * n / 256, ndot_total=1e52 * (n / 256) ** 3)
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------------- GPU arm
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_0908_2654_gb300.solver import Solver
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = args.size
+    w = workload(n)
+    cells = n**3
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(precision, steps, warmup, profile):
+        s = Solver(w, precision=precision, newton_tol=args.newton_tol, lin_rtol=args.lin_rtol, max_newton=40,
+                   max_lin=400, device=local_rank)
+        for _ in range(warmup):
+            s.step()
+        torch.cuda.synchronize()
+        if profile:
+            s.set_profiling(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local_rank) as clk:
+            e0.record(s.stream)
+            for _ in range(steps):
+                stats.append(s.step())
+            e1.record(s.stream)
+            torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        prof = s.profile() if profile else None
+        s.close()
+        return ms, stats, prof, clk.summary()
+
+    ms_mixed, st_mixed, prof, clocks = timed("mixed", args.steps, args.warmup, profile=True)
+    t = torch.tensor([ms_mixed], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * cells * args.steps / (ms_max * 1e-3)
+
+    fp64 = None
+    if not args.no_fp64:
+        ms64, st64, _, _ = timed("fp64", args.steps, args.warmup, profile=False)
+        t = torch.tensor([ms64], device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        v64 = world * cells * args.steps / (float(t.item()) * 1e-3)
+        fp64 = {"value": v64, "ms_per_step": float(t.item()) / args.steps,
+                "newton_iters": [x["newton_iters"] for x in st64], "linear_iters": [x["linear_iters"] for x in st64],
+                "speedup_mixed_vs_fp64": value / v64}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, w, local_rank, barrier, world)
+
+    return dict(value=value, ms=ms_max, stats=st_mixed, prof=prof, clocks=clocks, fp64=fp64, e2e=e2e, w=w)
+
+
+def run_e2e(args, w, local_rank, barrier, world):
+    """Same steps through the C ABI with host arrays: the step's inputs are copied from pinned host
+    memory and the result read back inside the timed region."""
+    import torch
+
+    from paper_0908_2654_gb300.solver import Solver
+
+    s = Solver(w, precision="mixed", newton_tol=args.newton_tol, lin_rtol=args.lin_rtol, max_newton=40,
+               max_lin=400, device=local_rank)
+    # the state lives in host memory between steps: E, n_HI and e_h go in and come back out
+    host_in = {k: getattr(s, k).cpu().pin_memory() for k in ("E", "nHI", "rho", "e_h", "clump")}
+    host_v = [v.cpu().pin_memory() for v in s.v]
+    out = {k: host_in[k] for k in ("E", "nHI", "e_h")}
+    out["ec"] = torch.empty_like(s.ec, device="cpu").pin_memory()
+    bi = sum(t.numel() * t.element_size() for t in list(host_in.values()) + host_v)
+    bo = sum(t.numel() * t.element_size() for t in out.values())
+    stream = s.stream
+
+    def one():
+        with torch.cuda.stream(stream):
+            for k, t in host_in.items():
+                getattr(s, k).copy_(t, non_blocking=True)
+            for dv, hv in zip(s.v, host_v):
+                dv.copy_(hv, non_blocking=True)
+        s.step()
+        with torch.cuda.stream(stream):
+            for k, t in out.items():
+                t.copy_(getattr(s, k), non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(max(1, args.warmup)):
+        one()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        one()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    s.close()
+    cells = w["nx"] * w["ny"] * w["nz"]
+    return {"value": world * cells * args.steps / (ms * 1e-3), "unit": "cell-steps/s",
+            "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+
+def oracle_sample(w, m, seed_corner=(0, 0, 0)):
+    """An m^3 periodic sub-block of workload w (its fields and the sources inside it)."""
+    z0, y0, x0 = seed_corner
+    sl = (slice(z0, z0 + m), slice(y0, y0 + m), slice(x0, x0 + m))
+    shape = (w["nz"], w["ny"], w["nx"])
+    zc, yc, xc = np.unravel_index(w["src_index"], shape)
+    inside = (zc >= z0) & (zc < z0 + m) & (yc >= y0) & (yc < y0 + m) & (xc >= x0) & (xc < x0 + m)
+    sub = dict(w)
+    sub.update(nx=m, ny=m, nz=m, periodic=(True, True, True),
+               rho_b=w["rho_b"][sl].copy(), T0=w["T0"][sl].copy(), v=tuple(v[sl].copy() for v in w["v"]),
+               clump=w["clump"][sl].copy(), E=w["E"][sl].copy(), nHI=w["nHI"][sl].copy(),
+               src_index=np.ravel_multi_index((zc[inside] - z0, yc[inside] - y0, xc[inside] - x0), (m, m, m)),
+               src_ndot=np.asarray(w["src_ndot"])[inside])
+    return sub
+
+
+def densest_corner(w, m):
+    """Corner of the m^3 block holding the most sources (so the sample contains fronts)."""
+    shape = (w["nz"], w["ny"], w["nx"])
+    zc, yc, xc = np.unravel_index(w["src_index"], shape)
+    best, corner = -1, (0, 0, 0)
+    for z0 in range(0, shape[0] - m + 1, m):
+        for y0 in range(0, shape[1] - m + 1, m):
+            for x0 in range(0, shape[2] - m + 1, m):
+                c = int(np.sum((zc >= z0) & (zc < z0 + m) & (yc >= y0) & (yc < y0 + m) & (xc >= x0) & (xc < x0 + m)))
+                if c > best:
+                    best, corner = c, (z0, y0, x0)
+    return corner
+
+
+def time_oracle_steps(w, m, nsteps, tol):
+    from oracle import driver
+    sub = oracle_sample(w, m, densest_corner(w, m))
+    r = driver.Run(sub)
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        r.advance(tol=tol)
+    dt = time.perf_counter() - t0
+    return m**3 * nsteps / dt, dt, int(len(sub["src_index"]))
+
+
+def cpu_baseline(w, tol):
+    m = 24
+    value, secs, nsrc = time_oracle_steps(w, m, 1, tol)
+    return {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"one implicit step of a {m}^3 periodic sub-block of the {w['nx']}^3 field "
+                      f"({nsrc} sources inside), FP64 numpy/SciPy oracle, single thread, {secs:.1f} s"}
+
+
+def run_reference(args):
+    n = args.size
+    w = workload(n)
+    m = 16
+    for _ in range(args.warmup):
+        time_oracle_steps(w, m, 1, args.newton_tol)
+    value, secs, nsrc = time_oracle_steps(w, m, args.steps, args.newton_tol)
+    cpu = {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+           "sample": f"{args.steps} implicit steps of a {m}^3 periodic sub-block of the {n}^3 field "
+                     f"({nsrc} sources), FP64 numpy/SciPy oracle, single thread"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"reionization-like field {n}^3 (oracle on {m}^3 sub-blocks)", "grid": n},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res = run_gpu(args, rank, world, local_rank)
+    if rank != 0:
+        return
+    peaks = load_peaks()
+    prof = res["prof"] or {}
+    dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
+    roof = None
+    if dom is not None:
+        per_launch_ms = dom["ms"] / dom["launches"]
+        per_launch_bytes = dom["bytes"] / dom["launches"]
+        achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+        peak = (peaks or {}).get("hbm_gbs", 6800.0)
+        roof = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s",
+                "share_of_step": dom["ms"] / res["ms"]}
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                   "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None,
+                   "share": v["ms"] / res["ms"]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+    launches = sum(x["kernel_launches"] for x in res["stats"]) + len(res["stats"])
+    w_desc = f"reionization-like field {args.size}^3, 2000 sources, z=9, dt=1 Myr, theta=1"
+    line = {
+        "metric": METRIC, "value": res["value"], "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": w_desc, "grid": args.size, "precision": "mixed (FP32 multigrid in FP64 Newton/CG)",
+                   "newton_tol": args.newton_tol, "lin_rtol": args.lin_rtol, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (each FP64 field 134 MB at 256^3)"},
+        "newton_iters": [x["newton_iters"] for x in res["stats"]],
+        "linear_iters": [x["linear_iters"] for x in res["stats"]],
+        "fp64": res["fp64"],
+        "roofline": roof,
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "clocks": res["clocks"],
+        "e2e": res["e2e"],
+    }
+    if not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline(res["w"], args.newton_tol)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * rt.h -- C ABI of the GB300 implicit radiation / ionisation / heating solver.
+ *
+ * The library advances one operator-split step (v) of Norman, Reynolds & So,
+ * "Cosmological Radiation Hydrodynamics with Enzo" (Sec. "Algorithm",
+ * subsection "Operator-Split Hydrodynamics with Radiative Feedback"): it solves
+ * the coupled system of Eqs. RT-cons_energy, RT-chemical_ionization and
+ * RT-cons_radiation for U = (e_c, n_HI, E) on a uniform Cartesian grid by
+ * driving the residual of Eqs. gas_residual, chemistry_residual and
+ * radiation_residual to zero with a globalised inexact Newton method.  Each
+ * Newton system is reduced by a Schur complement to a modified radiation
+ * equation (a 7-point symmetric operator in E), solved by conjugate gradients
+ * preconditioned with geometric multigrid.  Hydrogen-only gas (N_s = 1).
+ *
+ * Units.  All fields are in the paper's normalised comoving variables
+ * (Eqs. units, scalings, proper_vars): x~ = x/u_x, t~ = t/u_t, rho~ = rho/u_d,
+ * e~ = e/u_v^2, E~ = E/u_E with u_d = u_g/u_x^3, u_v = u_x/u_t, u_E = u_d u_v^2;
+ * number densities n~ = n/u_n with u_n = u_d/m_H (so n~_H = rho~ for X = 1).
+ * E and n are comoving densities (proper = comoving / a^3), v_b is the proper
+ * peculiar velocity.  Source rates are photons per second (physical).
+ *
+ * Memory.  Every array argument is a DEVICE pointer to a contiguous FP64 array
+ * of nx*ny*nz values in [z][y][x] order (x fastest) unless stated otherwise,
+ * owned by the caller.  The library owns its workspace (allocated in
+ * rt_init_grid, freed in rt_destroy_grid) and enqueues all work on the stream
+ * given in the descriptor; every call returns after synchronising that stream.
+ *
+ * Errors.  Functions return RT_OK (0) or one of the positive codes below; no C++
+ * exception crosses the ABI.  On any error the caller's output arrays are left
+ * unchanged; rt_error_string() gives a message.  The last error's detail text is
+ * available from rt_last_error_detail().
+ */
+#ifndef RT_H
+#define RT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RT_OK 0
+#define RT_EINVAL 1        /* invalid argument or grid shape                         */
+#define RT_ENOMEM 2        /* device allocation failed                               */
+#define RT_ECUDA 3         /* a CUDA call failed                                     */
+#define RT_ENOCONV 4       /* Newton did not reach newton_tol within max_newton      */
+#define RT_ELINESEARCH 5   /* backtracking could not reduce the residual norm        */
+#define RT_ENONFINITE 6    /* a residual or linear-solver quantity became NaN/Inf    */
+#define RT_ELINEAR 7       /* the linear solver did not reach lin_rtol in max_lin    */
+
+enum { RT_BC_PERIODIC = 0, RT_BC_WALL = 1 };            /* per axis; WALL = zero flux   */
+enum { RT_FP64 = 0, RT_MIXED = 1 };                     /* multigrid precision          */
+enum { RT_SPECTRUM_MONO = 0, RT_SPECTRUM_BLACKBODY = 1 };
+enum { RT_RECOMB_CONST = 0, RT_RECOMB_HG97 = 1 };
+enum { RT_LIMITER_LAGGED = 0, RT_LIMITER_CONST = 1 };
+
+/* Grid and solver description (rt_init_grid copies it). */
+typedef struct {
+    int nx, ny, nz;       /* cells per axis; each level coarsened by 2 while all dims are even
+                             and the level has more cells than the coarse-level bound (4096
+                             FP32 / 2048 FP64); a level above that bound with an odd dim is
+                             rejected with RT_EINVAL                                         */
+    double dx;            /* comoving cell width, normalised (cm / u_x)                     */
+    int bc[3];            /* boundary per axis (x, y, z): RT_BC_PERIODIC or RT_BC_WALL        */
+    double u_x, u_t, u_g; /* unit factors of Eq. units: cm, s, g                               */
+    double theta;         /* two-level time parameter of Eq. radiation_residual (paper: 0.51) */
+    int precision;        /* RT_FP64 or RT_MIXED (FP32 multigrid inside FP64 Newton/CG)       */
+    int isothermal;       /* 1: T = T_iso and f_e = e_c                                        */
+    double T_iso;         /* K                                                               */
+    int spectrum;         /* RT_SPECTRUM_MONO (13.6 eV) or RT_SPECTRUM_BLACKBODY              */
+    double T_B;           /* blackbody temperature, K                                        */
+    int recomb;           /* RT_RECOMB_CONST (alpha_B = 2.59e-13) or RT_RECOMB_HG97           */
+    int cooling;          /* non-isothermal runs: 1 = include Lambda                          */
+    int limiter;          /* RT_LIMITER_LAGGED (Eq. limiter at the step's start state) or
+                             RT_LIMITER_CONST (D = D_const, a test mode)                      */
+    double D_const;       /* proper diffusion coefficient for RT_LIMITER_CONST, cm^2/s        */
+    double E_min;         /* radiation floor of the limiter and rate smoothing, erg/cm^3
+                             (paper's initial value 1e-35); 0 selects 1e-35                  */
+    double newton_tol;    /* RMS norm (Eq. rmsnorm, component-scaled) at which Newton stops   */
+    int max_newton;       /* Newton iterations per step                                      */
+    double lin_rtol;      /* relative reduction of the weighted Schur residual per solve      */
+    int max_lin;          /* CG iterations per Newton system                                 */
+    int mg_nu1, mg_nu2;   /* red-black Gauss-Seidel sweeps before / after coarse correction  */
+    int device;           /* CUDA device ordinal                                             */
+    void* stream;         /* cudaStream_t to enqueue on (NULL = legacy default stream)       */
+} rt_grid_desc;
+
+/* Per-step inputs from the rest of the operator split (steps (i)-(iv)); device pointers. */
+typedef struct {
+    const double* rho_b;  /* comoving baryon density (normalised)                            */
+    const double* e_h;    /* specific total gas energy after hydro (normalised)              */
+    const double* vx;     /* proper peculiar velocity components (normalised); NULL = 0      */
+    const double* vy;
+    const double* vz;
+    const float* clump;   /* clumping factor on the recombination term; NULL = 1             */
+    double a, adot, dt;   /* expansion factor, da/dt~ and step length in normalised time     */
+    int nsrc;             /* number of point sources                                         */
+    const int64_t* src_cell;  /* DEVICE: flat [z][y][x] index of each source's cell          */
+    const double* src_ndot;   /* DEVICE: ionising photons per second of each source           */
+} rt_step_inputs;
+
+/* Caller-owned state, device pointers, normalised units. */
+typedef struct {
+    double* E;            /* radiation energy density                                        */
+    double* n_HI;         /* neutral hydrogen number density                                 */
+    double* e_c;          /* gas energy correction of step (v) (specific)                    */
+} rt_state;
+
+#define RT_STATS_HIST 64
+typedef struct {
+    int newton_iters;     /* accepted Newton updates                                         */
+    int residual_evals;   /* fused residual/Jacobian evaluations (incl. rejected trials)     */
+    int linear_iters;     /* CG iterations summed over the step                              */
+    int line_search_cuts; /* step halvings                                                   */
+    double norm0;         /* RMS norm of f at the initial iterate                            */
+    double norm;          /* RMS norm of f at the returned state                             */
+    int kernel_launches;  /* kernels this call launched                                      */
+    int nhist;            /* entries used in the histories below                             */
+    double hist_norm[RT_STATS_HIST];  /* per evaluation: RMS norm (trial norms use the weights
+                                         of the current iterate)                             */
+    double hist_lam[RT_STATS_HIST];   /* per evaluation: step length of the trial (0 = start) */
+    int hist_cg[RT_STATS_HIST];       /* per Newton iteration: CG iterations (negative when the
+                                         requested reduction was not reached)                 */
+} rt_step_stats;
+
+typedef struct rt_grid rt_grid;   /* opaque */
+
+/* Allocate workspace and precompute the grey spectral constants (Eq. grey_definition) and
+ * unit factors.  *out receives the handle.  Errors: RT_EINVAL (shape, units, parameters),
+ * RT_ENOMEM, RT_ECUDA. */
+int rt_init_grid(const rt_grid_desc* desc, rt_grid** out);
+
+/* One implicit step (v): on entry *inout holds the advected state (E*, n_HI*; e_c is
+ * ignored and taken as 0), on success it holds U^{n+1} with f(U^{n+1}) below newton_tol.
+ * stats may be NULL.  Errors: RT_EINVAL, RT_ENOCONV, RT_ELINESEARCH, RT_ENONFINITE,
+ * RT_ELINEAR, RT_ECUDA; *inout is unchanged on error. */
+int rt_implicit_step(rt_grid* g, const rt_step_inputs* in, rt_state* inout, rt_step_stats* stats);
+
+/* Residual f(U) = (f_e, f_n, f_E) of Eqs. gas_residual, chemistry_residual,
+ * radiation_residual at the iterate U for the step that starts from U_n (E*, n_HI*).
+ * Outputs are caller device arrays.  Errors: RT_EINVAL, RT_ECUDA. */
+int rt_residual(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U,
+                double* f_e, double* f_n, double* f_E);
+
+/* Schur complement of the Newton system at U (Sec. "Algorithm": the reduction to a modified
+ * radiation equation): S = J_EE - J_Eu J_uu^-1 J_uE as diag (per cell) and the three +x/+y/+z
+ * face couplings w (S_ij = -w on the face between i and its + neighbour; S is symmetric), and
+ * rhs = -f_E + J_Eu J_uu^-1 f_u.  The operator is also kept as the one rt_schur_solve uses.
+ * Errors: RT_EINVAL, RT_ECUDA. */
+int rt_schur_system(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U,
+                    double* diag, double* wx, double* wy, double* wz, double* rhs);
+
+/* Solve S x = b for the operator of the last rt_schur_system call with multigrid-
+ * preconditioned conjugate gradients (multigrid in the grid's precision) until the
+ * residual's 2-norm falls below rtol times ||b||_2.  x: initial guess in, solution out.
+ * *iters receives the CG iterations.  Errors: RT_EINVAL, RT_ELINEAR, RT_ENONFINITE, RT_ECUDA. */
+int rt_schur_solve(rt_grid* g, const double* b, double* x, double rtol, int max_iters, int* iters);
+
+/* Operator-split hand-over between steps without hydrodynamics: e_h += e_c (device arrays of
+ * nx*ny*nz values).  Errors: RT_EINVAL, RT_ECUDA. */
+int rt_fold_energy(rt_grid* g, double* e_h, const double* e_c);
+
+/* Per-kernel timing.  While enabled, every kernel the library launches is bracketed by CUDA
+ * events on the grid's stream and its algorithmic bytes (the arrays it must read and write,
+ * counted once per launch) are recorded; rt_get_profile returns the totals per kernel class
+ * accumulated since the last enable.  Timing adds two events per launch.  Errors: RT_EINVAL. */
+typedef struct {
+    char name[32];        /* kernel class                                                    */
+    int launches;         /* launches recorded                                               */
+    double ms;            /* summed event time of those launches                             */
+    double bytes;         /* summed algorithmic bytes of those launches                      */
+} rt_kernel_profile;
+int rt_set_profiling(rt_grid* g, int on);
+int rt_get_profile(rt_grid* g, rt_kernel_profile* out, int max_entries, int* n_entries);
+
+/* Discrete adjoint of one step (not available in this version: returns RT_EINVAL). */
+int rt_adjoint_step(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U_np1,
+                    const rt_state* lam_np1, rt_state* lam_n, double* g_ndot, float* g_clump);
+
+void rt_destroy_grid(rt_grid* g);
+const char* rt_error_string(int code);
+const char* rt_last_error_detail(void);
+
+/* Grey constants the library derived at init, in CGS: sigma_E [cm^2], sigma_G [cm^2/erg],
+ * eps_src [erg] (Eq. grey_definition with sigma ~ nu^-3).  Errors: RT_EINVAL. */
+int rt_grey_constants(const rt_grid* g, double* sigma_E, double* sigma_G, double* eps_src);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -290,13 +290,24 @@ def E_FLOOR_INT():
     return K.K_BOLTZ / ((K.GAMMA - 1.0) * K.M_H)
 
 
+E_REL_FLOOR = 1e-12
+
+
+def weight_floor_E(st):
+    """Smallest E scale the norm resolves: max(E_min, 1e-12 max_cells(E^n + dt 4 pi eta)),
+    fixed for the step.  Radiation twelve orders of magnitude below the brightest cell of
+    the step does not ionise anything within dt; asking for per-cell relative accuracy
+    there is below the rounding left by the bright cells."""
+    return max(st.E_min, E_REL_FLOOR * float(np.max(np.abs(st.E_n + st.dt * emissivity(st)))))
+
+
 def weights(st, U):
     """Per-component scales of the residual norm (w_e, w_n, w_E) at the iterate U.
 
-    f_E / max(|E|, E^n, E_min), f_n / n_H, f_e / max(e_int of the hydro state, 1 K).
+    f_E / max(|E|, E^n, E_floor), f_n / n_H, f_e / max(e_int of the hydro state, 1 K).
     """
     e_c, nHI, E = np.real(U)
-    wE = 1.0 / np.maximum(np.maximum(np.abs(E), st.E_n), st.E_min)
+    wE = 1.0 / np.maximum(np.maximum(np.abs(E), st.E_n), weight_floor_E(st))
     wn = 1.0 / st.n_H
     we = 1.0 / np.maximum(internal_energy_h(st), E_FLOOR_INT())
     return np.stack([we + 0 * E, wn + 0 * E, wE])

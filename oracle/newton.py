@@ -253,24 +253,30 @@ def solve_step(st, tol=1e-11, maxit=60, freeze=False, linear="auto", U0=None, ve
 
 def schur_system(st, U, bE=None):
     """(S, r): S = J_EE - J_Eu J_uu^-1 J_uE and r = -f_E + J_Eu J_uu^-1 f_u (sparse, N x N),
-    with J the linearisation that holds D fixed, u = (e_c, n_HI)."""
+    u = (e_c, n_HI).
+
+    The cell-local equations make J_uu block diagonal (one 2x2 block per cell, checked
+    here); its inverse is formed block by block with numpy and the products are sparse.
+    """
     if bE is None:
         bE = M.explicit_part(st)
     N = st.N
-    J = jacobian(st, U, bE, freeze=True).tocsc()
+    J = jacobian(st, U, bE, freeze=True).tocsr()
     f = M.residual(st, U, bE).reshape(_FIELDS, N)
-    Juu = J[: 2 * N, : 2 * N]
+    Juu = J[: 2 * N, : 2 * N].tocoo()
     JuE = J[: 2 * N, 2 * N:]
     JEu = J[2 * N:, : 2 * N]
     JEE = J[2 * N:, 2 * N:]
-    lu = spla.splu(Juu.tocsc())
-    X = lu.solve(JuE.toarray()) if N <= 4096 else None
-    if X is None:
-        # J_uu is block diagonal per cell; solve column blocks without densifying everything
-        X = sp.csc_matrix(spla.spsolve(Juu.tocsc(), JuE.tocsc()))
-        S = JEE - JEu @ X
-    else:
-        S = JEE - sp.csr_matrix(JEu @ X)
-    fu = f[:2].ravel()
-    r = -f[2] + JEu @ lu.solve(fu)
+    if np.any((Juu.row % N) != (Juu.col % N)):
+        raise AssertionError("J_uu couples different cells")
+    blocks = np.zeros((N, 2, 2))
+    np.add.at(blocks, (Juu.row % N, Juu.row // N, Juu.col // N), Juu.data)
+    inv = np.linalg.inv(blocks)
+    cells = np.arange(N)
+    rows = np.concatenate([a * N + cells for a in (0, 0, 1, 1)])
+    cols = np.concatenate([b * N + cells for b in (0, 1, 0, 1)])
+    vals = np.concatenate([inv[:, 0, 0], inv[:, 0, 1], inv[:, 1, 0], inv[:, 1, 1]])
+    Juu_inv = sp.csr_matrix((vals, (rows, cols)), shape=(2 * N, 2 * N))
+    S = JEE - JEu @ (Juu_inv @ JuE)
+    r = -f[2] + JEu @ (Juu_inv @ f[:2].ravel())
     return sp.csr_matrix(S), r

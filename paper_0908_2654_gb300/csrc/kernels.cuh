@@ -1,0 +1,122 @@
+// Kernel declarations and launch helpers shared by the host driver.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "physics.cuh"
+
+// Maximum cells of the level that the single-CTA coarse solver takes over.
+template <class T> struct TailMax;
+template <> struct TailMax<float> { static const int value = 4096; };
+template <> struct TailMax<double> { static const int value = 2048; };
+
+#define RT_RED_SLOTS 4      // simultaneous sums per reduction
+#define RT_MAX_PARTIALS 4096
+
+struct Dims {
+    int nx, ny, nz;
+    int per[3];
+    __host__ __device__ long long n() const { return (long long)nx * ny * nz; }
+};
+
+// ---- step setup
+void launch_zero(double* p, long long n, cudaStream_t s);
+void launch_scatter_sources(double* src, const int64_t* cell, const double* ndot, int nsrc, double scale,
+                            long long ncell, int* d_err, cudaStream_t s);
+void launch_faces(const PhysParams& P, const double* E0, const double* n0, double* wx, double* wy, double* wz,
+                  float* wxf, float* wyf, float* wzf, cudaStream_t s);
+// also writes per-block max |E_init| to partials (one slot); returns the number of blocks
+int launch_setup(const PhysParams& P, const double* E0, const double* n0, const double* src, const double* wx,
+                 const double* wy, const double* wz, double* bE, double* E_init, double* n_init, double* ec_init,
+                 double* partials, cudaStream_t s);
+
+// ---- fused Newton evaluation
+struct AssembleArgs {
+    // trial iterate: E_t = E_cur + lam * step (step may be null); u from local solve
+    const double* E_cur;
+    const double* step;
+    double lam;
+    const double* n_guess;   // local-solve starting values (current iterate)
+    const double* ec_guess;
+    // given-iterate mode (parity entry points): u is taken from here, no local solve
+    const double* n_given;
+    const double* ec_given;
+    // per-step data
+    const double* E0;
+    const double* n0;
+    const double* rho;
+    const double* e_h;
+    const double* vx;
+    const double* vy;
+    const double* vz;
+    const float* clump;
+    const double* bE;
+    const double* src;
+    const double* wx;
+    const double* wy;
+    const double* wz;
+    // outputs
+    double* E_out;
+    double* n_out;
+    double* ec_out;
+    double* diag;       // Schur diagonal
+    double* rhs;        // Schur right side
+    double* wE;         // norm weight of the trial (for the linear solver's residual norm)
+    double* fE_out;     // optional residual outputs (parity entry points)
+    double* fn_out;
+    double* fe_out;
+    double* partials;   // RT_RED_SLOTS * nblocks block sums
+};
+int launch_assemble(const PhysParams& P, const AssembleArgs& A, bool given_u, cudaStream_t s);
+
+// ---- reductions (deterministic: block partials then one ordered pass)
+void launch_finalize(const double* partials, int nblocks, int nslots, double* out, cudaStream_t s);
+// slots [0, nsum) are summed, slots [nsum, nsum + nmax) are maxima
+void launch_finalize_ext(const double* partials, int nblocks, int nsum, int nmax, double* out, cudaStream_t s);
+
+// ---- CG vector kernels (FP64)
+int launch_spmv_dot(const Dims& D, const double* diag, const double* wx, const double* wy, const double* wz,
+                     const double* p, double* q, double* partials, cudaStream_t s);
+int launch_residual_norm(const Dims& D, const double* diag, const double* wx, const double* wy, const double* wz,
+                         const double* b, const double* x, double* r, const double* w, double* partials,
+                         cudaStream_t s);
+int launch_cg_update_xr(long long n, const double* scal, double* x, double* r, const double* p, const double* q,
+                        const double* w, double* partials, cudaStream_t s);
+int launch_dot2(long long n, const double* z, const double* r, const double* q, double* partials, cudaStream_t s);
+void launch_p_update(long long n, const double* scal, const double* z, double* p, cudaStream_t s);
+void launch_cast_d2f(long long n, const double* a, float* b, cudaStream_t s);
+// b = a * 2^-k and back, with 2^k >= *amax (keeps an FP64 vector inside the FP32 range)
+void launch_cast_d2f_scaled(long long n, const double* a, float* b, const double* amax, cudaStream_t s);
+void launch_cast_f2d_scaled(long long n, const float* a, double* b, const double* amax, cudaStream_t s);
+// multigrid operator diagonal: max(diag, sum of the 6 face couplings), i.e. sigma = max(sigma, 0)
+template <class T>
+void launch_mg_diag(const Dims& D, const double* diag, const double* wx, const double* wy, const double* wz, T* out,
+                    cudaStream_t s);
+void launch_cast_f2d(long long n, const float* a, double* b, cudaStream_t s);
+void launch_copy(long long n, const double* a, double* b, cudaStream_t s);
+void launch_add(long long n, const double* a, double* b, cudaStream_t s);   // b += a
+// scalar bookkeeping on the device: scal[] holds alpha, beta and the dot products
+void launch_cg_scalars(double* scal, const double* dots, int phase, cudaStream_t s);
+
+// ---- multigrid (T = float or double)
+template <class T>
+struct Level {
+    Dims d;
+    T* diag;
+    T* wx;
+    T* wy;
+    T* wz;
+    T* x;
+    T* b;
+};
+template <class T>
+void launch_coarsen(const Level<T>& f, const Level<T>& c, cudaStream_t s);
+template <class T>
+void launch_rbgs(const Level<T>& L, int color, bool zero_guess, cudaStream_t s);
+template <class T>
+void launch_resid_restrict(const Level<T>& f, const Level<T>& c, cudaStream_t s);
+template <class T>
+void launch_prolong_add(const Level<T>& c, const Level<T>& f, cudaStream_t s);
+template <class T>
+int launch_tail(const Level<T>& L, int ncycles, int nu, cudaStream_t s);
+template <class T>
+size_t tail_smem_bytes(const Dims& d);

@@ -1,0 +1,358 @@
+// Per-step and per-Newton-iteration kernels of the implicit step (FP64).
+//
+//  k_faces       once per step: flux-limited face couplings w = dt theta D / (a dx)^2 on the
+//                +x/+y/+z face of every cell, D from Eq. limiter at the step's starting state.
+//  k_setup       once per step: explicit part b_E of Eq. radiation_residual and the initial
+//                iterate (E* + dt 4 pi eta, n_HI*, 0).
+//  k_assemble    once per Newton trial, fused: trial E = E_k + lam s, exact solution of the
+//                cell-local equations for (e_c, n_HI) at that E (with forward-mode
+//                derivatives), radiation residual f_E (7-point), Schur diagonal and right side
+//                of the reduced Newton system (Sec. "Algorithm"), and the block partial sums of
+//                the component-scaled RMS norm (Eq. rmsnorm).
+#include "kernels.cuh"
+
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ void cell_coords(long long i, int nx, int ny, int& x, int& y, int& z) {
+    long long q = i / nx;
+    x = (int)(i - q * nx);
+    z = (int)(q / ny);
+    y = (int)(q - (long long)z * ny);
+}
+
+// neighbour index along an axis; at a wall the index is clamped (its face coupling is 0)
+__device__ __forceinline__ int up(int c, int n, int per) { return c + 1 < n ? c + 1 : (per ? 0 : c); }
+__device__ __forceinline__ int dn(int c, int n, int per) { return c > 0 ? c - 1 : (per ? n - 1 : c); }
+
+template <int NS>
+__device__ void block_sums(double (&v)[NS], double* partials) {
+    __shared__ double sh[NS][kBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        double s = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[k][warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NS) {
+        double s = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) s += sh[threadIdx.x][w];
+        partials[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+__global__ void k_zero(double* p, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = 0.0;
+}
+
+__global__ void k_scatter(double* src, const int64_t* cell, const double* ndot, int nsrc, double scale,
+                          long long ncell, int* err) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nsrc) return;
+    long long c = cell[k];
+    if (c < 0 || c >= ncell) {      // checked: an out-of-range source index is reported, not written
+        atomicExch(err, 1);
+        return;
+    }
+    atomicAdd(&src[c], scale * ndot[k]);
+}
+
+__global__ void k_faces(PhysParams P, const double* __restrict__ E0, const double* __restrict__ n0,
+                        double* __restrict__ wx, double* __restrict__ wy, double* __restrict__ wz,
+                        float* __restrict__ wxf, float* __restrict__ wyf, float* __restrict__ wzf) {
+    const long long n = (long long)P.nx * P.ny * P.nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        cell_coords(i, P.nx, P.ny, x, y, z);
+        const double Ei = E0[i];
+        const double ki = P.kE * n0[i] / P.a3;
+        const long long sy = P.nx, sz = (long long)P.nx * P.ny;
+        const long long base = i - x - (long long)y * sy - (long long)z * sz;
+        long long j[3] = {base + up(x, P.nx, P.per[0]) + y * sy + z * sz,
+                          base + x + up(y, P.ny, P.per[1]) * sy + z * sz,
+                          base + x + y * sy + up(z, P.nz, P.per[2]) * sz};
+        const bool wall[3] = {!P.per[0] && x == P.nx - 1, !P.per[1] && y == P.ny - 1, !P.per[2] && z == P.nz - 1};
+        double w[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (wall[d]) {
+                w[d] = 0.0;
+            } else {
+                const double D = limiter_face(P, Ei, E0[j[d]], ki, P.kE * n0[j[d]] / P.a3);
+                w[d] = P.wscale * D;
+            }
+        }
+        wx[i] = w[0];
+        wy[i] = w[1];
+        wz[i] = w[2];
+        if (wxf) {
+            wxf[i] = (float)w[0];
+            wyf[i] = (float)w[1];
+            wzf[i] = (float)w[2];
+        }
+    }
+}
+
+struct Stencil {
+    long long xm, xp, ym, yp, zm, zp;
+    double wxm, wxp, wym, wyp, wzm, wzp;
+};
+
+__device__ __forceinline__ Stencil stencil(long long i, int x, int y, int z, int nx, int ny, int nz, const int* per,
+                                           const double* __restrict__ wx, const double* __restrict__ wy,
+                                           const double* __restrict__ wz) {
+    Stencil s;
+    const long long sy = nx, sz = (long long)nx * ny;
+    const long long b = i - x - (long long)y * sy - (long long)z * sz;
+    s.xm = b + dn(x, nx, per[0]) + y * sy + z * sz;
+    s.xp = b + up(x, nx, per[0]) + y * sy + z * sz;
+    s.ym = b + x + dn(y, ny, per[1]) * sy + z * sz;
+    s.yp = b + x + up(y, ny, per[1]) * sy + z * sz;
+    s.zm = b + x + y * sy + dn(z, nz, per[2]) * sz;
+    s.zp = b + x + y * sy + up(z, nz, per[2]) * sz;
+    s.wxp = wx[i];
+    s.wyp = wy[i];
+    s.wzp = wz[i];
+    s.wxm = (!per[0] && x == 0) ? 0.0 : wx[s.xm];
+    s.wym = (!per[1] && y == 0) ? 0.0 : wy[s.ym];
+    s.wzm = (!per[2] && z == 0) ? 0.0 : wz[s.zm];
+    return s;
+}
+
+__global__ void k_setup(PhysParams P, const double* __restrict__ E0, const double* __restrict__ n0,
+                        const double* __restrict__ src, const double* __restrict__ wx, const double* __restrict__ wy,
+                        const double* __restrict__ wz, double* __restrict__ bE, double* __restrict__ E_init,
+                        double* __restrict__ n_init, double* __restrict__ ec_init, double* partials) {
+    const long long n = (long long)P.nx * P.ny * P.nz;
+    const double expl = (1.0 - P.theta) / P.theta;   // (1-theta) dt D/(a dx)^2 = expl * w
+    double emax = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        cell_coords(i, P.nx, P.ny, x, y, z);
+        const Stencil s = stencil(i, x, y, z, P.nx, P.ny, P.nz, P.per, wx, wy, wz);
+        const double E = E0[i];
+        const double lap = s.wxp * (E0[s.xp] - E) + s.wxm * (E0[s.xm] - E) + s.wyp * (E0[s.yp] - E) +
+                           s.wym * (E0[s.ym] - E) + s.wzp * (E0[s.zp] - E) + s.wzm * (E0[s.zm] - E);
+        const double kap = P.kE * n0[i] / P.a3;
+        bE[i] = E + expl * lap + P.dt * (1.0 - P.theta) * (-P.H * E + src[i] - P.c * kap * E);
+        const double Ei = E + P.dt * src[i];
+        E_init[i] = Ei;
+        n_init[i] = n0[i];
+        ec_init[i] = 0.0;
+        emax = fmax(emax, fabs(Ei));
+    }
+    __shared__ double sh[kBlock / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = emax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) m = fmax(m, sh[w]);
+        partials[blockIdx.x] = m;
+    }
+}
+
+// Local equations f_e = e_c - S_e, f_n = n - S_n at fixed E: solution, residual and the
+// pieces of the Schur reduction, X = (J_uu^-1 J_uE)_n and Y = (J_uu^-1 f_u)_n.
+struct LocalOut {
+    double ec, n, fe, fn, X, Y;
+};
+
+template <bool ISO, bool GIVEN>
+__device__ __forceinline__ LocalOut local_block(const PhysParams& P, const CellIn& c, double E, double ec_in,
+                                                double n_in, double se) {
+    LocalOut o;
+    if (ISO) {
+        Dual<1> Se, Sn;
+        local_solutions<Dual<1>>(P, c, dconst<1>(0.0), dconst<1>(n_in), dvar<1>(E, 0), Se, Sn);
+        o.ec = GIVEN ? ec_in : 0.0;
+        o.n = GIVEN ? n_in : Sn.v;
+        o.fe = o.ec;
+        o.fn = o.n - Sn.v;
+        o.X = -Sn.d[0];
+        o.Y = o.fn;
+        return o;
+    }
+    double ec = ec_in, n = n_in;
+    if (!GIVEN) n = fmin(fmax(n, 1e-300), c.rho);
+    const int maxit = GIVEN ? 1 : 24;
+    for (int it = 0; it < maxit; ++it) {
+        Dual<3> Se, Sn;
+        local_solutions<Dual<3>>(P, c, dvar<3>(ec, 0), dvar<3>(n, 1), dvar<3>(E, 2), Se, Sn);
+        const double fe = ec - Se.v, fn = n - Sn.v;
+        const double a11 = 1.0 - Se.d[0], a12 = -Se.d[1], a21 = -Sn.d[0], a22 = 1.0 - Sn.d[1];
+        const double be = -Se.d[2], bn = -Sn.d[2];
+        const double det = a11 * a22 - a12 * a21;
+        o.ec = ec;
+        o.n = n;
+        o.fe = fe;
+        o.fn = fn;
+        o.X = (a11 * bn - a21 * be) / det;
+        o.Y = (a11 * fn - a21 * fe) / det;
+        if (GIVEN) break;
+        const double de = -(a22 * fe - a12 * fn) / det;
+        const double dn_ = -(a11 * fn - a21 * fe) / det;
+        if (fabs(de) <= 1e-15 * se && fabs(dn_) <= 1e-15 * c.rho) break;
+        ec += de;
+        n = fmin(fmax(n + dn_, 1e-300), c.rho);
+    }
+    return o;
+}
+
+template <bool ISO, bool GIVEN>
+__global__ void __launch_bounds__(kBlock) k_assemble(PhysParams P, AssembleArgs A) {
+    const long long n = (long long)P.nx * P.ny * P.nz;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        cell_coords(i, P.nx, P.ny, x, y, z);
+        const Stencil s = stencil(i, x, y, z, P.nx, P.ny, P.nz, P.per, A.wx, A.wy, A.wz);
+        const double lam = A.lam;
+        const double* Ec = A.E_cur;
+        const double* st = A.step;
+        auto Et = [&](long long j) { return st ? fma(lam, st[j], Ec[j]) : Ec[j]; };
+        const double E = Et(i);
+        const double lap = s.wxp * (Et(s.xp) - E) + s.wxm * (Et(s.xm) - E) + s.wyp * (Et(s.yp) - E) +
+                           s.wym * (Et(s.ym) - E) + s.wzp * (Et(s.zp) - E) + s.wzm * (Et(s.zm) - E);
+        const double sumw = s.wxp + s.wxm + s.wyp + s.wym + s.wzp + s.wzm;
+
+        CellIn c;
+        c.rho = A.rho[i];
+        c.nHI0 = A.n0[i];
+        c.E0 = A.E0[i];
+        double v2 = 0.0;
+        if (A.vx) v2 += A.vx[i] * A.vx[i];
+        if (A.vy) v2 += A.vy[i] * A.vy[i];
+        if (A.vz) v2 += A.vz[i] * A.vz[i];
+        c.eh_kin = A.e_h[i] - 0.5 * v2;
+        c.clump = A.clump ? (double)A.clump[i] : 1.0;
+        const double se = fmax(c.eh_kin, P.e_floor);
+
+        const double ec_in = GIVEN ? A.ec_given[i] : (A.ec_guess ? A.ec_guess[i] : 0.0);
+        const double n_in = GIVEN ? A.n_given[i] : A.n_guess[i];
+        const LocalOut L = local_block<ISO, GIVEN>(P, c, E, ec_in, n_in, se);
+
+        const double kap = P.kE * L.n / P.a3;
+        const double dtt = P.dt * P.theta;
+        const double fE = E - A.bE[i] - lap - dtt * (-P.H * E + A.src[i] - P.c * kap * E);
+        const double AEn = dtt * P.c * P.kE * E / P.a3;
+        const double AEE = 1.0 + dtt * (P.H + P.c * kap) + sumw;
+        const double dg = AEE - AEn * L.X;
+        const double rh = -fE + AEn * L.Y;
+
+        const double wEc = 1.0 / fmax(fmax(fabs(Ec[i]), c.E0), P.E_floor);
+        const double wEt = 1.0 / fmax(fmax(fabs(E), c.E0), P.E_floor);
+        const double loc = (L.fn / c.rho) * (L.fn / c.rho) + (L.fe / se) * (L.fe / se);
+        acc[0] += (wEc * fE) * (wEc * fE) + loc;
+        acc[1] += (wEt * fE) * (wEt * fE) + loc;
+        if (!isfinite(fE) || !isfinite(dg) || !isfinite(L.n) || !isfinite(L.ec)) acc[2] += 1.0;
+
+        if (A.E_out) A.E_out[i] = E;
+        if (A.n_out) A.n_out[i] = L.n;
+        if (A.ec_out) A.ec_out[i] = L.ec;
+        if (A.diag) A.diag[i] = dg;
+        if (A.rhs) A.rhs[i] = rh;
+        if (A.wE) A.wE[i] = wEt;
+        if (A.fE_out) A.fE_out[i] = fE;
+        if (A.fn_out) A.fn_out[i] = L.fn;
+        if (A.fe_out) A.fe_out[i] = L.fe;
+    }
+    block_sums<3>(acc, A.partials);
+}
+
+__global__ void k_finalize(const double* __restrict__ partials, int nblocks, int nslots, double* out) {
+    __shared__ double sh[256];
+    for (int k = 0; k < nslots; ++k) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[(size_t)k * nblocks + b];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[k] = sh[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_finalize_ext(const double* __restrict__ partials, int nblocks, int nsum, int nmax, double* out) {
+    __shared__ double sh[256];
+    for (int k = 0; k < nsum + nmax; ++k) {
+        const bool is_max = k >= nsum;
+        double s = is_max ? 0.0 : 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+            const double v = partials[(size_t)k * nblocks + b];
+            s = is_max ? fmax(s, v) : s + v;
+        }
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) sh[threadIdx.x] = is_max ? fmax(sh[threadIdx.x], sh[threadIdx.x + w])
+                                                          : sh[threadIdx.x] + sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[k] = sh[0];
+        __syncthreads();
+    }
+}
+
+int grid_for(long long n) {
+    long long b = (n + kBlock - 1) / kBlock;
+    const long long cap = 152LL * 8;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+void launch_zero(double* p, long long n, cudaStream_t s) { k_zero<<<grid_for(n), kBlock, 0, s>>>(p, n); }
+
+void launch_scatter_sources(double* src, const int64_t* cell, const double* ndot, int nsrc, double scale,
+                            long long ncell, int* d_err, cudaStream_t s) {
+    if (nsrc <= 0) return;
+    k_scatter<<<(nsrc + 255) / 256, 256, 0, s>>>(src, cell, ndot, nsrc, scale, ncell, d_err);
+}
+
+void launch_faces(const PhysParams& P, const double* E0, const double* n0, double* wx, double* wy, double* wz,
+                  float* wxf, float* wyf, float* wzf, cudaStream_t s) {
+    const long long n = (long long)P.nx * P.ny * P.nz;
+    k_faces<<<grid_for(n), kBlock, 0, s>>>(P, E0, n0, wx, wy, wz, wxf, wyf, wzf);
+}
+
+int launch_setup(const PhysParams& P, const double* E0, const double* n0, const double* src, const double* wx,
+                 const double* wy, const double* wz, double* bE, double* E_init, double* n_init, double* ec_init,
+                 double* partials, cudaStream_t s) {
+    const long long n = (long long)P.nx * P.ny * P.nz;
+    const int g = grid_for(n);
+    k_setup<<<g, kBlock, 0, s>>>(P, E0, n0, src, wx, wy, wz, bE, E_init, n_init, ec_init, partials);
+    return g;
+}
+
+int launch_assemble(const PhysParams& P, const AssembleArgs& A, bool given_u, cudaStream_t s) {
+    const long long n = (long long)P.nx * P.ny * P.nz;
+    const int g = grid_for(n);
+    if (P.isothermal) {
+        if (given_u) k_assemble<true, true><<<g, kBlock, 0, s>>>(P, A);
+        else k_assemble<true, false><<<g, kBlock, 0, s>>>(P, A);
+    } else {
+        if (given_u) k_assemble<false, true><<<g, kBlock, 0, s>>>(P, A);
+        else k_assemble<false, false><<<g, kBlock, 0, s>>>(P, A);
+    }
+    return g;
+}
+
+void launch_finalize(const double* partials, int nblocks, int nslots, double* out, cudaStream_t s) {
+    k_finalize<<<1, 256, 0, s>>>(partials, nblocks, nslots, out);
+}
+
+void launch_finalize_ext(const double* partials, int nblocks, int nsum, int nmax, double* out, cudaStream_t s) {
+    k_finalize_ext<<<1, 256, 0, s>>>(partials, nblocks, nsum, nmax, out);
+}

@@ -1,0 +1,152 @@
+// Cell-local physics of step (v) in normalised units, templated on double / Dual<K>.
+//
+//  * flux limiter on a face (Eq. limiter), evaluated at the step's starting state;
+//  * S_n: exact solution over dt of the hydrogen rate equation (Eq. RT-chemical_ionization
+//    with n_e = n_HII = n_H - n_HI) with its coefficients frozen -- a Riccati equation
+//    n' = A (n_H - n)^2 - G n, solved in Bernoulli form about its equilibrium root;
+//  * S_e: exact solution of de/dt = -2 (adot/a) e + (G - Lambda) with frozen G - Lambda
+//    and e_c^n = 0 (Eq. RT-cons_energy);
+//  * rates: constant case-B alpha = 2.59e-13 cm^3/s or the Hui & Gnedin (1997) fit,
+//    photo-heating n_HI c E (sigma_E - h nu_0 sigma_G), cooling by case-B recombination
+//    (Hui & Gnedin 1997), collisional excitation and bremsstrahlung (Cen 1992) and
+//    Compton scattering off the CMB.
+#pragma once
+#include "dual.cuh"
+
+struct PhysParams {
+    // grid
+    int nx, ny, nz;
+    int per[3];
+    double dx;         // comoving cell width (normalised)
+    // step
+    double a, a3, H;   // expansion factor, a^3, adot / a (per normalised time)
+    double dt, theta;
+    double wscale;     // dt * theta / (a dx)^2: face coupling w = wscale * D
+    double adx;        // proper cell width a dx
+    // constants in normalised units
+    double c;          // speed of light
+    double kE;         // kappa = kE n / a^3        (proper opacity per normalised length)
+    double kG;         // Gamma = kG Ebar / a^3     (photo-ionisation rate)
+    double kA;         // A = alpha[cm^3/s] kA C / a^3  (recombination coefficient of n)
+    double kH;         // heating per unit mass = kH n Ebar / (a^3 rho)
+    double kC;         // cooling per unit mass = kC a^3 Lambda_vol[cgs] / rho
+    double kT;         // T = kT e_int rho / (2 rho - n)   [K]
+    double un;         // u_n [cm^-3]: proper physical density = n un / a^3
+    double E_min;      // radiation floor (limiter, rate smoothing)
+    double E_floor;    // per step: smallest E scale of the residual norm, max(E_min, 1e-12 max E_init)
+    double e_floor;    // specific internal energy of 1 K gas (mu = 1), for the norm
+    double phi_e;      // dt * phi1(2 H dt): S_e = (G - Lambda) phi_e
+    double T_iso;
+    double D_const;    // normalised proper diffusion coefficient (limiter "const")
+    double src_scale;  // 4 pi eta = src_scale * Ndot in the source's cell
+    double alpha_const;
+    int isothermal, recomb, cooling, limiter;
+};
+
+#define RT_T_HI 157807.0
+#define RT_T_FLOOR 1.0
+
+// smooth positive part (x + sqrt(x^2 + eps^2)) / 2, written without cancellation for x < 0
+template <class T>
+RT_HD T spos(const T& x, double eps) {
+    T r = sqrt(x * x + eps * eps);
+    if (value(x) < 0.0) return (eps * eps) / (2.0 * (r - x));
+    return 0.5 * (x + r);
+}
+
+// (1 - e^-x) / x with its limit 1 at x = 0
+template <class T>
+RT_HD T phi1(const T& x) {
+    if (fabs(value(x)) < 1e-8) return 1.0 - x * 0.5 + x * x * (1.0 / 6.0);
+    return -expm1(-x) / x;
+}
+
+// n(dt) for n' = A (nH - n)^2 - G n, n(0) = y0.
+// The right side is A (n - y_eq)(n - y_2) with y_eq = 2 A nH^2 / (2 A nH + G + d),
+// d = sqrt(G^2 + 4 A G nH) = A (y_2 - y_eq).  u = n - y_eq obeys u' = A u^2 - d u, so
+// u(t) = u0 e^{-d t} / (1 - u0 A t phi1(d t)).
+template <class T>
+RT_HD T riccati_n(double y0, double nH, const T& A, const T& G, double dt) {
+    T d = sqrt(G * G + 4.0 * nH * (A * G));
+    T den = 2.0 * nH * A + G + d;
+    T yeq = (value(den) > 0.0) ? (2.0 * nH * nH) * A / den : den * 0.0;
+    T u0 = y0 - yeq;
+    T x = d * dt;
+    T q = exp(-x);
+    return yeq + u0 * q / (1.0 - (u0 * A) * (dt * phi1(x)));
+}
+
+// case-B recombination coefficient [cm^3/s], Hui & Gnedin (1997)
+template <class T>
+RT_HD T alpha_hg97(const T& temp) {
+    T lam = (2.0 * RT_T_HI) / temp;
+    return 2.753e-14 * pow(lam, 1.5) / pow(1.0 + pow(lam * (1.0 / 2.740), 0.407), 2.242);
+}
+
+// cooling per unit proper volume [erg cm^-3 s^-1] from proper densities [cm^-3]
+template <class T>
+RT_HD T cooling_volume(const T& temp, const T& ne, const T& nHI, const T& nHII, double a) {
+    T lam = (2.0 * RT_T_HI) / temp;
+    T rec = 3.435e-30 * temp * pow(lam, 1.970) / pow(1.0 + pow(lam * (1.0 / 2.250), 0.376), 3.720);
+    T ce = 7.5e-19 * exp(-118348.0 / temp) / (1.0 + sqrt(temp * 1e-5));
+    T lt = log(temp) * (1.0 / 2.302585092994046);   // log10 T
+    T dl = 5.5 - lt;
+    T gff = 1.1 + 0.34 * exp(dl * dl * (-1.0 / 3.0));
+    T ff = 1.42e-27 * gff * sqrt(temp);
+    const double Tcmb = 2.725 / a;
+    // 4 k_B sigma_T a_rad / (m_e c) [erg cm^-3... per K^5 n_e] (CGS constants)
+    const double kcomp = 4.0 * 1.380649e-16 * 6.6524587321e-25 * 7.565723e-15 / (9.1093837015e-28 * 2.99792458e10);
+    T comp = kcomp * (Tcmb * Tcmb) * (Tcmb * Tcmb) * (temp - Tcmb);
+    return (rec * nHII + ff * nHII + ce * nHI + comp) * ne;
+}
+
+// Cell inputs that do not depend on the iterate.
+struct CellIn {
+    double rho;     // n_H (= rho~ in these units)
+    double nHI0;    // n_HI at the start of the step
+    double E0;      // E at the start of the step
+    double eh_kin;  // e_h - |v|^2 / 2 (specific internal energy from the hydro state)
+    double clump;
+};
+
+// S_e and S_n at the iterate (ec, n, E) with coefficients frozen at that iterate.
+template <class T>
+RT_HD void local_solutions(const PhysParams& P, const CellIn& c, const T& ec, const T& n, const T& E,
+                           T& Se, T& Sn) {
+    T Ebar = spos(P.theta * E + (1.0 - P.theta) * c.E0, P.E_min);
+    T G = (P.kG / P.a3) * Ebar;
+    T temp;
+    if (P.isothermal) {
+        temp = ec * 0.0 + P.T_iso;
+    } else {
+        temp = (P.kT * c.rho) * (c.eh_kin + ec) / (2.0 * c.rho - n);
+        if (value(temp) < RT_T_FLOOR) temp = temp * 0.0 + RT_T_FLOOR;
+    }
+    T alpha = (P.recomb == 0) ? temp * 0.0 + P.alpha_const : alpha_hg97(temp);
+    T A = alpha * (P.kA * c.clump / P.a3);
+    Sn = riccati_n(c.nHI0, c.rho, A, G, P.dt);
+    if (P.isothermal) {
+        Se = ec * 0.0;
+        return;
+    }
+    T heat = (P.kH / (P.a3 * c.rho)) * (n * Ebar);
+    T cool = heat * 0.0;
+    if (P.cooling) {
+        const double s = P.un / P.a3;
+        T nHII = (c.rho - n) * s;
+        T nHIp = n * s;
+        cool = (P.kC * P.a3 / c.rho) * cooling_volume(temp, nHII, nHIp, nHII, P.a);
+    }
+    Se = (heat - cool) * P.phi_e;
+}
+
+// Eq. limiter on a face between cells with energies (Ei, Ej) and proper opacities
+// (ki, kj); R from the face difference over the proper width, E_face = spos(mean E).
+RT_HD double limiter_face(const PhysParams& P, double Ei, double Ej, double ki, double kj) {
+    if (P.limiter == 1) return P.D_const;
+    double Ef = spos(0.5 * (Ei + Ej), P.E_min);
+    double R = fabs(Ej - Ei) / (P.adx * Ef);
+    double kT = 0.5 * (ki + kj);
+    if (kT == 0.0 && R == 0.0) R = 1.0 / P.adx;
+    return P.c * (2.0 * kT + R) / ((6.0 * kT + 3.0 * R) * kT + R * R);
+}

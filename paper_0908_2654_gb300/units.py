@@ -1,0 +1,56 @@
+"""Unit normalisation of the paper (Eqs. units, scalings, proper_vars) for the Python side.
+
+x~ = x/u_x, t~ = t/u_t, rho~ = rho/u_d, e~ = e/u_v^2, E~ = E/u_E, n~ = n/u_n with
+u_d = u_g/u_x^3, u_v = u_x/u_t, u_E = u_d u_v^2 and u_n = u_d/m_H (hydrogen-only gas,
+so n~_H = rho~).  Also the equation of state used to turn a temperature into the
+specific total gas energy e_h (Eqs. eos, temperature: T = (gamma-1) e_int rho /(k_B n_tot)).
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+K_B = 1.380649e-16
+M_H = 1.6735575e-24
+GAMMA = 5.0 / 3.0
+MYR = 3.15576e13
+
+
+@dataclass
+class Units:
+    u_x: float   # cm
+    u_t: float   # s
+    u_g: float   # g
+
+    @property
+    def u_d(self):
+        return self.u_g / self.u_x**3
+
+    @property
+    def u_v(self):
+        return self.u_x / self.u_t
+
+    @property
+    def u_E(self):
+        return self.u_d * self.u_v**2
+
+    @property
+    def u_n(self):
+        return self.u_d / M_H
+
+    @staticmethod
+    def for_grid(dx_cm, rho_mean, u_t=MYR):
+        """Length unit = cell width, time unit = 1 Myr, density unit = mean baryon density."""
+        return Units(u_x=dx_cm, u_t=u_t, u_g=rho_mean * dx_cm**3)
+
+
+def specific_energy(T, rho_b, nHI, v):
+    """e_h [erg/g] of gas at temperature T with neutral density nHI (X = 1) moving with v."""
+    nH = rho_b / M_H
+    e_int = K_B * T * (2.0 * nH - nHI) / ((GAMMA - 1.0) * rho_b)
+    return e_int + 0.5 * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2)
+
+
+def temperature(e_total, rho_b, nHI, v):
+    nH = rho_b / M_H
+    e_int = e_total - 0.5 * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2)
+    return (GAMMA - 1.0) * e_int * rho_b / (K_B * (2.0 * nH - nHI))

@@ -1,0 +1,56 @@
+"""The C-ABI library builds for sm_103a and exports every function include/rt.h declares.
+
+No compute calls are made (no GPU is needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rt.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rt_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_0908_2654_gb300 import _rt
+    if not os.path.exists(_rt.LIB_PATH):
+        import importlib
+        importlib.import_module("paper_0908_2654_gb300.build").build()
+    return _rt.LIB_PATH
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("rt_init_grid", "rt_implicit_step", "rt_adjoint_step", "rt_destroy_grid", "rt_error_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (rt_[a-z_0-9]+)\b", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_binding_loads_and_error_strings(libpath):
+    from paper_0908_2654_gb300 import _rt
+    try:
+        L = _rt.lib()
+    except OSError as e:   # the CUDA runtime may be absent on a machine without a driver
+        pytest.skip(f"library not loadable here: {e}")
+    for name in declared_functions():
+        assert hasattr(L, name)
+    assert L.rt_error_string(_rt.RT_ENOCONV).decode().startswith("Newton")
+    assert _rt.GridDesc in (type(_rt.GridDesc()),)
+    # the ctypes mirrors have the field order of the header structs
+    hdr = open(HEADER).read()
+    for field in ("newton_tol", "lin_rtol", "mg_nu1", "stream"):
+        assert field in hdr and field in [f for f, _ in _rt.GridDesc._fields_]
