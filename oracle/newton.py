@@ -174,11 +174,13 @@ def initial_iterate(st):
     return np.stack([np.zeros(st.shape), st.nHI_n.copy(), st.E_n + st.dt * M.emissivity(st)])
 
 
-def local_solve(st, U, tol=1e-15, maxit=30):
+def local_solve(st, U, tol=1e-14, maxit=60):
     """Solve the cell-local equations f_e = f_n = 0 for (e_c, n_HI) at fixed E.
 
-    Isothermal runs: e_c = 0 and n_HI = S_n(E) directly.  Otherwise a per-cell
-    2x2 Newton iteration with complex-step derivatives.
+    Isothermal runs: e_c = 0 and n_HI = S_n(E) directly.  Otherwise a per-cell damped
+    2x2 Newton iteration with complex-step derivatives: each step is halved until the
+    scaled local residual max(|f_e|/e_int, |f_n|/n_H) decreases, keeping 0 < n_HI <= n_H
+    and the internal energy positive.
     """
     e_c, nHI, E = (np.array(x, float) for x in U)
     if st.isothermal:
@@ -186,19 +188,48 @@ def local_solve(st, U, tol=1e-15, maxit=30):
     h = 1e-30
     se = np.maximum(M.internal_energy_h(st), M.E_FLOOR_INT())
     sn = st.n_H
+    eint_h = M.internal_energy_h(st)
+
+    def scaled(fe, fn):
+        return np.maximum(np.abs(fe) / se, np.abs(fn) / sn)
+
+    nHI = np.clip(nHI, 1e-300, st.n_H)
+    fe, fn = (np.real(x) for x in M.local_residual(st, e_c, nHI, E))
+    r = scaled(fe, fn)
     for _ in range(maxit):
-        fe, fn = M.local_residual(st, e_c, nHI, E)
+        active = r > tol
+        if not np.any(active):
+            break
         fe1, fn1 = M.local_residual(st, e_c + 1j * h * se, nHI, E)
         fe2, fn2 = M.local_residual(st, e_c, nHI + 1j * h * sn, E)
         a11, a21 = np.imag(fe1) / (h * se), np.imag(fn1) / (h * se)
         a12, a22 = np.imag(fe2) / (h * sn), np.imag(fn2) / (h * sn)
         det = a11 * a22 - a12 * a21
-        de = -(a22 * fe - a12 * fn) / det
-        dn = -(-a21 * fe + a11 * fn) / det
-        e_c = e_c + de
-        nHI = np.clip(nHI + dn, 1e-300, st.n_H)
-        if np.max(np.abs(de) / se) < tol and np.max(np.abs(dn) / sn) < tol:
-            break
+        de = np.where(active, -(a22 * fe - a12 * fn) / det, 0.0)
+        dn = np.where(active, -(-a21 * fe + a11 * fn) / det, 0.0)
+        lam = np.ones_like(e_c)
+        todo = active.copy()
+        for _ in range(40):
+            ec_t = e_c + lam * de
+            # keep the internal energy positive and the neutral density inside (0, n_H]
+            ec_t = np.maximum(ec_t, -0.999 * eint_h)
+            n_t = np.clip(nHI + lam * dn, 1e-300, st.n_H)
+            fe_t, fn_t = (np.real(x) for x in M.local_residual(st, ec_t, n_t, E))
+            r_t = scaled(fe_t, fn_t)
+            ok = todo & (r_t < r)
+            e_c = np.where(ok, ec_t, e_c)
+            nHI = np.where(ok, n_t, nHI)
+            fe = np.where(ok, fe_t, fe)
+            fn = np.where(ok, fn_t, fn)
+            r = np.where(ok, r_t, r)
+            todo &= ~ok
+            if not np.any(todo):
+                break
+            lam = np.where(todo, 0.5 * lam, lam)
+        if np.any(todo & (r > 1e-9)):
+            # no decrease along the Newton direction: the cell sits at its round-off floor
+            # or needs more iterations; leave it for the next outer iteration
+            pass
     return np.stack([e_c, nHI, E])
 
 

@@ -102,6 +102,8 @@ T* dalloc(size_t n, bool& ok) {
         ok = false;
         return nullptr;
     }
+    // workspace starts at zero so that no run depends on what earlier allocations left behind
+    if (cudaMemset(p, 0, n * sizeof(T)) != cudaSuccess) ok = false;
     return static_cast<T*>(p);
 }
 
@@ -359,7 +361,10 @@ int pcg(rt_grid* g, const double* b, double* x, const double* w, double rtol, in
         *iters = k;
         const double rn = std::sqrt(v[0]);
         if (!std::isfinite(rn)) {
-            set_detail("non-finite residual in CG iteration %d", k);
+            double sc[4] = {0, 0, 0, 0};
+            cudaMemcpy(sc, g->scal, sizeof(sc), cudaMemcpyDeviceToHost);
+            set_detail("non-finite residual in CG iteration %d (alpha %g, beta %g, (z,r) %g, (p,q) %g, |r0| %g)", k,
+                       sc[0], sc[1], sc[2], sc[3], rn0);
             return RT_ENONFINITE;
         }
         if (rn <= rtol * rn0) return RT_OK;
@@ -770,7 +775,11 @@ int rt_implicit_step(rt_grid* g, const rt_step_inputs* in, rt_state* io, rt_step
         rc = pcg(g, g->rhs, g->step, g->wE, g->desc.lin_rtol, g->desc.max_lin, &its);
         st.linear_iters += its;
         if (st.newton_iters < RT_STATS_HIST) st.hist_cg[st.newton_iters] = rc == RT_OK ? its : -its;
-        if (rc && rc != RT_ELINEAR) return rc;   // a failed reduction still gives a usable direction
+        if (rc && rc != RT_ELINEAR) {             // a failed reduction still gives a usable direction
+            st.kernel_launches = g->launches;
+            if (stats) *stats = st;
+            return rc;
+        }
         lam = 1.0;
     }
     st.kernel_launches = g->launches;

@@ -402,17 +402,29 @@ __host__ __device__ inline void make_plan(const Dims& top, TailPlan& p) {
     p.dense = (last.n() > 1 && last.n() <= kDenseMax) ? 1 : 0;
 }
 
+// one colour of a red-black Gauss-Seidel sweep on a shared-memory level: the new value is
+// (b + sum of the neighbours' couplings) / diag; the cell's own previous value is not read
 template <class T>
 __device__ void tail_smooth(const Dims& d, T* diag, T* wx, T* wy, T* wz, T* x, const T* b, int color, bool zero) {
     const long long n = d.n();
+    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
     for (long long i = threadIdx.x; i < n; i += blockDim.x) {
         int cx, cy, cz;
         cell_coords(i, d.nx, d.ny, cx, cy, cz);
         if (((cx + cy + cz) & 1) != color) continue;
         T num = b[i];
         if (!zero) {
-            const T v = apply_S<T, T>(i, cx, cy, cz, d, diag, wx, wy, wz, x);   // diag x - off
-            num += diag[i] * x[i] - v;
+            const long long b0 = i - cx - (long long)cy * sy - (long long)cz * sz;
+            const long long xm = b0 + dn(cx, d.nx, d.per[0]) + cy * sy + cz * sz;
+            const long long xp = b0 + up(cx, d.nx, d.per[0]) + cy * sy + cz * sz;
+            const long long ym = b0 + cx + dn(cy, d.ny, d.per[1]) * sy + cz * sz;
+            const long long yp = b0 + cx + up(cy, d.ny, d.per[1]) * sy + cz * sz;
+            const long long zm = b0 + cx + cy * sy + dn(cz, d.nz, d.per[2]) * sz;
+            const long long zp = b0 + cx + cy * sy + up(cz, d.nz, d.per[2]) * sz;
+            const T wxm = (!d.per[0] && cx == 0) ? T(0) : wx[xm];
+            const T wym = (!d.per[1] && cy == 0) ? T(0) : wy[ym];
+            const T wzm = (!d.per[2] && cz == 0) ? T(0) : wz[zm];
+            num += wx[i] * x[xp] + wxm * x[xm] + wy[i] * x[yp] + wym * x[ym] + wz[i] * x[zp] + wzm * x[zm];
         }
         x[i] = num / diag[i];
     }
@@ -437,8 +449,9 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(Level<T> L, int ncycles, 
         swy[i] = L.wy[i];
         swz[i] = L.wz[i];
         sb[i] = L.b[i];
-        sx[i] = T(0);
     }
+    // every level's iterate starts at zero: shared memory holds whatever an earlier kernel left
+    for (int i = threadIdx.x; i < tot; i += blockDim.x) sx[i] = T(0);
     __syncthreads();
     for (int l = 1; l < plan.nlev; ++l) {
         const Dims& cd = plan.d[l];

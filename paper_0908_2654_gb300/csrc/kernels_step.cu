@@ -179,29 +179,53 @@ __device__ __forceinline__ LocalOut local_block(const PhysParams& P, const CellI
         o.Y = o.fn;
         return o;
     }
+    // damped 2x2 Newton: steps are halved until max(|f_e|/e_int, |f_n|/n_H) decreases,
+    // keeping 0 < n_HI <= n_H and the internal energy positive
     double ec = ec_in, n = n_in;
     if (!GIVEN) n = fmin(fmax(n, 1e-300), c.rho);
-    const int maxit = GIVEN ? 1 : 24;
-    for (int it = 0; it < maxit; ++it) {
-        Dual<3> Se, Sn;
-        local_solutions<Dual<3>>(P, c, dvar<3>(ec, 0), dvar<3>(n, 1), dvar<3>(E, 2), Se, Sn);
-        const double fe = ec - Se.v, fn = n - Sn.v;
+    Dual<3> Se, Sn;
+    local_solutions<Dual<3>>(P, c, dvar<3>(ec, 0), dvar<3>(n, 1), dvar<3>(E, 2), Se, Sn);
+    double fe = ec - Se.v, fn = n - Sn.v;
+    double r = fmax(fabs(fe) / se, fabs(fn) / c.rho);
+    const int maxit = GIVEN ? 0 : 60;
+    for (int it = 0; it < maxit && r > 1e-14; ++it) {
         const double a11 = 1.0 - Se.d[0], a12 = -Se.d[1], a21 = -Sn.d[0], a22 = 1.0 - Sn.d[1];
-        const double be = -Se.d[2], bn = -Sn.d[2];
         const double det = a11 * a22 - a12 * a21;
-        o.ec = ec;
-        o.n = n;
-        o.fe = fe;
-        o.fn = fn;
-        o.X = (a11 * bn - a21 * be) / det;
-        o.Y = (a11 * fn - a21 * fe) / det;
-        if (GIVEN) break;
         const double de = -(a22 * fe - a12 * fn) / det;
         const double dn_ = -(a11 * fn - a21 * fe) / det;
-        if (fabs(de) <= 1e-15 * se && fabs(dn_) <= 1e-15 * c.rho) break;
-        ec += de;
-        n = fmin(fmax(n + dn_, 1e-300), c.rho);
+        double lam = 1.0;
+        bool moved = false;
+        for (int k = 0; k < 40; ++k, lam *= 0.5) {
+            const double ec_t = fmax(ec + lam * de, -0.999 * c.eh_kin);
+            const double n_t = fmin(fmax(n + lam * dn_, 1e-300), c.rho);
+            Dual<3> Se_t, Sn_t;
+            local_solutions<Dual<3>>(P, c, dvar<3>(ec_t, 0), dvar<3>(n_t, 1), dvar<3>(E, 2), Se_t, Sn_t);
+            const double fe_t = ec_t - Se_t.v, fn_t = n_t - Sn_t.v;
+            const double r_t = fmax(fabs(fe_t) / se, fabs(fn_t) / c.rho);
+            if (r_t < r) {
+                ec = ec_t;
+                n = n_t;
+                Se = Se_t;
+                Sn = Sn_t;
+                fe = fe_t;
+                fn = fn_t;
+                r = r_t;
+                moved = true;
+                break;
+            }
+        }
+        if (!moved) break;   // round-off floor
     }
+    const double a11 = 1.0 - Se.d[0], a21 = -Sn.d[0];
+    const double a12 = -Se.d[1], a22 = 1.0 - Sn.d[1];
+    const double det = a11 * a22 - a12 * a21;
+    const double be = -Se.d[2], bn = -Sn.d[2];
+    o.ec = ec;
+    o.n = n;
+    o.fe = fe;
+    o.fn = fn;
+    o.X = (a11 * bn - a21 * be) / det;
+    o.Y = (a11 * fn - a21 * fe) / det;
     return o;
 }
 

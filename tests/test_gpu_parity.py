@@ -167,7 +167,10 @@ def _step_both(name, w, nsteps, precision, tol=1e-11):
     s = _solver(w, precision=precision, newton_tol=tol, lin_rtol=1e-12, max_newton=60, max_lin=300)
     worst = {"E": 0.0, "n": 0.0, "e": 0.0}
     for st, U, e_h_next in traj:
-        stats = s.step()
+        try:
+            stats = s.step()
+        except RuntimeError as e:
+            raise AssertionError(f"{e}; history {getattr(e, 'stats', None)}") from e
         ec, n, E = s.state_cgs()
         wE = 1.0 / np.maximum(np.maximum(np.abs(U[2]), st.E_n), st.E_min)
         worst["E"] = max(worst["E"], float(np.max(np.abs(E - U[2]) * wE)))
