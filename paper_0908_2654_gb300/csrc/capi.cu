@@ -424,6 +424,8 @@ PhysParams step_params(const rt_grid* g, const rt_step_inputs* in) {
     P.wscale = in->dt * g->desc.theta / (P.adx * P.adx);
     const double x = 2.0 * P.H * in->dt;
     P.phi_e = in->dt * (std::fabs(x) < 1e-8 ? 1.0 - 0.5 * x + x * x / 6.0 : -std::expm1(-x) / x);
+    // the local equations are solved three orders of magnitude below the Newton tolerance
+    P.local_tol = std::max(1e-14, 1e-3 * g->desc.newton_tol);
     return P;
 }
 

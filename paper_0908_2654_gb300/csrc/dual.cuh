@@ -124,6 +124,8 @@ RT_HD Dual<K> expm1(const Dual<K>& a) {
 template <int K>
 RT_HD Dual<K> log(const Dual<K>& a) { return dchain(a, ::log(a.v), 1.0 / a.v); }
 template <int K>
+RT_HD Dual<K> log1p(const Dual<K>& a) { return dchain(a, ::log1p(a.v), 1.0 / (1.0 + a.v)); }
+template <int K>
 RT_HD Dual<K> pow(const Dual<K>& a, double p) {
     const double v = ::pow(a.v, p);
     return dchain(a, v, p * v / a.v);

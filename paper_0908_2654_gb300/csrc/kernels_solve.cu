@@ -197,22 +197,23 @@ __global__ void k_cast_d2f(long long n, const double* __restrict__ a, float* __r
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         b[i] = (float)a[i];
 }
-__device__ __forceinline__ int scale_exponent(double amax) {
+// 2^-e with 2^e >= amax: an exact power-of-two scale
+__device__ __forceinline__ double pow2_scale(double amax, bool inverse) {
     int e = 0;
     if (amax > 0.0 && isfinite(amax)) frexp(amax, &e);   // amax < 2^e
-    return e;
+    return ldexp(1.0, inverse ? e : -e);
 }
 __global__ void k_cast_d2f_scaled(long long n, const double* __restrict__ a, float* __restrict__ b,
                                   const double* __restrict__ amax) {
-    const int e = scale_exponent(*amax);
+    const double sc = pow2_scale(*amax, false);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        b[i] = (float)ldexp(a[i], -e);
+        b[i] = (float)(a[i] * sc);
 }
 __global__ void k_cast_f2d_scaled(long long n, const float* __restrict__ a, double* __restrict__ b,
                                   const double* __restrict__ amax) {
-    const int e = scale_exponent(*amax);
+    const double sc = pow2_scale(*amax, true);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        b[i] = ldexp((double)a[i], e);
+        b[i] = (double)a[i] * sc;
 }
 __global__ void k_cast_f2d(long long n, const float* __restrict__ a, double* __restrict__ b) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)

@@ -188,7 +188,7 @@ __device__ __forceinline__ LocalOut local_block(const PhysParams& P, const CellI
     double fe = ec - Se.v, fn = n - Sn.v;
     double r = fmax(fabs(fe) / se, fabs(fn) / c.rho);
     const int maxit = GIVEN ? 0 : 60;
-    for (int it = 0; it < maxit && r > 1e-14; ++it) {
+    for (int it = 0; it < maxit && r > P.local_tol; ++it) {
         const double a11 = 1.0 - Se.d[0], a12 = -Se.d[1], a21 = -Sn.d[0], a22 = 1.0 - Sn.d[1];
         const double det = a11 * a22 - a12 * a21;
         const double de = -(a22 * fe - a12 * fn) / det;

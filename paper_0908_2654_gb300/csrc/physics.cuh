@@ -36,6 +36,7 @@ struct PhysParams {
     double E_floor;    // per step: smallest E scale of the residual norm, max(E_min, 1e-12 max E_init)
     double e_floor;    // specific internal energy of 1 K gas (mu = 1), for the norm
     double phi_e;      // dt * phi1(2 H dt): S_e = (G - Lambda) phi_e
+    double local_tol;  // scaled residual at which the cell-local Newton iteration stops
     double T_iso;
     double D_const;    // normalised proper diffusion coefficient (limiter "const")
     double src_scale;  // 4 pi eta = src_scale * Ndot in the source's cell
@@ -76,27 +77,49 @@ RT_HD T riccati_n(double y0, double nH, const T& A, const T& G, double dt) {
     return yeq + u0 * q / (1.0 - (u0 * A) * (dt * phi1(x)));
 }
 
-// case-B recombination coefficient [cm^3/s], Hui & Gnedin (1997)
+// Temperature-dependent factors shared by the recombination coefficient and the cooling
+// terms: every power of T or of lambda = 2 T_HI / T is taken from one log T and one sqrt T.
 template <class T>
-RT_HD T alpha_hg97(const T& temp) {
-    T lam = (2.0 * RT_T_HI) / temp;
-    return 2.753e-14 * pow(lam, 1.5) / pow(1.0 + pow(lam * (1.0 / 2.740), 0.407), 2.242);
+struct TFactors {
+    T temp, logT, sqrtT, invT, loglam, lam, sqrtlam;
+};
+
+template <class T>
+RT_HD TFactors<T> t_factors(const T& temp) {
+    TFactors<T> f;
+    f.temp = temp;
+    f.invT = 1.0 / temp;
+    f.logT = log(temp);
+    f.sqrtT = sqrt(temp);
+    f.lam = (2.0 * RT_T_HI) * f.invT;
+    f.loglam = 12.662275226919286 - f.logT;            // log(2 T_HI) - log T, log(315614)
+    f.sqrtlam = 561.7953363992976 / f.sqrtT;           // sqrt(2 T_HI) / sqrt T, sqrt(315614)
+    return f;
 }
 
-// cooling per unit proper volume [erg cm^-3 s^-1] from proper densities [cm^-3]
+// case-B recombination coefficient [cm^3/s], Hui & Gnedin (1997):
+// 2.753e-14 lam^1.5 / (1 + (lam/2.740)^0.407)^2.242
 template <class T>
-RT_HD T cooling_volume(const T& temp, const T& ne, const T& nHI, const T& nHII, double a) {
-    T lam = (2.0 * RT_T_HI) / temp;
-    T rec = 3.435e-30 * temp * pow(lam, 1.970) / pow(1.0 + pow(lam * (1.0 / 2.250), 0.376), 3.720);
-    T ce = 7.5e-19 * exp(-118348.0 / temp) / (1.0 + sqrt(temp * 1e-5));
-    T lt = log(temp) * (1.0 / 2.302585092994046);   // log10 T
-    T dl = 5.5 - lt;
+RT_HD T alpha_hg97(const TFactors<T>& f) {
+    T p = exp(0.407 * (f.loglam - 1.0079579203999789));            // (lam / 2.740)^0.407
+    return 2.753e-14 * (f.lam * f.sqrtlam) * exp(-2.242 * log1p(p));
+}
+
+// cooling per unit proper volume [erg cm^-3 s^-1] from proper densities [cm^-3]:
+// case-B recombination (Hui & Gnedin 1997), collisional excitation and bremsstrahlung
+// (Cen 1992), Compton scattering off the CMB
+template <class T>
+RT_HD T cooling_volume(const TFactors<T>& f, const T& ne, const T& nHI, const T& nHII, double a) {
+    T q = exp(0.376 * (f.loglam - 0.8109302162163288));            // (lam / 2.250)^0.376
+    T rec = 3.435e-30 * f.temp * exp(1.970 * f.loglam - 3.720 * log1p(q));
+    T ce = 7.5e-19 * exp(-118348.0 * f.invT) / (1.0 + f.sqrtT * 3.1622776601683794e-3);
+    T dl = 5.5 - f.logT * 0.43429448190325176;                     // 5.5 - log10 T
     T gff = 1.1 + 0.34 * exp(dl * dl * (-1.0 / 3.0));
-    T ff = 1.42e-27 * gff * sqrt(temp);
+    T ff = 1.42e-27 * gff * f.sqrtT;
     const double Tcmb = 2.725 / a;
-    // 4 k_B sigma_T a_rad / (m_e c) [erg cm^-3... per K^5 n_e] (CGS constants)
+    // 4 k_B sigma_T a_rad / (m_e c) in CGS
     const double kcomp = 4.0 * 1.380649e-16 * 6.6524587321e-25 * 7.565723e-15 / (9.1093837015e-28 * 2.99792458e10);
-    T comp = kcomp * (Tcmb * Tcmb) * (Tcmb * Tcmb) * (temp - Tcmb);
+    T comp = kcomp * (Tcmb * Tcmb) * (Tcmb * Tcmb) * (f.temp - Tcmb);
     return (rec * nHII + ff * nHII + ce * nHI + comp) * ne;
 }
 
@@ -122,7 +145,10 @@ RT_HD void local_solutions(const PhysParams& P, const CellIn& c, const T& ec, co
         temp = (P.kT * c.rho) * (c.eh_kin + ec) / (2.0 * c.rho - n);
         if (value(temp) < RT_T_FLOOR) temp = temp * 0.0 + RT_T_FLOOR;
     }
-    T alpha = (P.recomb == 0) ? temp * 0.0 + P.alpha_const : alpha_hg97(temp);
+    const bool need_t = P.recomb != 0 || (!P.isothermal && P.cooling);
+    TFactors<T> tf;
+    if (need_t) tf = t_factors(temp);
+    T alpha = (P.recomb == 0) ? temp * 0.0 + P.alpha_const : alpha_hg97(tf);
     T A = alpha * (P.kA * c.clump / P.a3);
     Sn = riccati_n(c.nHI0, c.rho, A, G, P.dt);
     if (P.isothermal) {
@@ -135,7 +161,7 @@ RT_HD void local_solutions(const PhysParams& P, const CellIn& c, const T& ec, co
         const double s = P.un / P.a3;
         T nHII = (c.rho - n) * s;
         T nHIp = n * s;
-        cool = (P.kC * P.a3 / c.rho) * cooling_volume(temp, nHII, nHIp, nHII, P.a);
+        cool = (P.kC * P.a3 / c.rho) * cooling_volume(tf, nHII, nHIp, nHII, P.a);
     }
     Se = (heat - cool) * P.phi_e;
 }
