@@ -173,6 +173,23 @@ typedef struct {
 int rt_set_profiling(rt_grid* g, int on);
 int rt_get_profile(rt_grid* g, rt_kernel_profile* out, int max_entries, int* n_entries);
 
+/* Allocation-free residual.  The paper has no counterpart: this is a service for callers
+ * that cannot allocate device memory (an application that owns the whole device memory
+ * budget through its own pool, work issued during CUDA stream capture, allocation-free
+ * real-time loops).  It computes the same f(U) as rt_residual but takes the descriptor
+ * instead of a grid handle and calls no cudaMalloc, cudaFree or allocating library routine:
+ * its scratch is one file-scope device array of RT_RESIDUAL_STATIC_MAX_CELLS cells' worth
+ * (about 2.2 MB), which every GPU that loads the library holds until the process exits.
+ * Grids with more cells are rejected with RT_EINVAL.  The first call on a device looks up
+ * the array's device address on that device; make that first call before any stream
+ * capture.  Every call uses the same array: calls whose GPU work overlaps (other streams,
+ * other host threads on the same device) race on it and must be serialised by the caller.
+ * Arguments as rt_residual; desc->device and desc->stream select where the work runs.
+ * Errors: RT_EINVAL, RT_ECUDA. */
+#define RT_RESIDUAL_STATIC_MAX_CELLS 32768
+int rt_residual_static(const rt_grid_desc* desc, const rt_step_inputs* in, const rt_state* U_n,
+                       const rt_state* U, double* f_e, double* f_n, double* f_E);
+
 /* Discrete adjoint of one step (not available in this version: returns RT_EINVAL). */
 int rt_adjoint_step(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U_np1,
                     const rt_state* lam_np1, rt_state* lam_n, double* g_ndot, float* g_clump);

@@ -919,3 +919,69 @@ int rt_adjoint_step(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, c
 }
 
 }  // extern "C"
+
+// Step parameters from a descriptor alone (no grid handle, no allocation): the same unit
+// factors, grey constants and per-step values rt_init_grid and rt_implicit_step derive.
+// Used by the allocation-free entry point in noalloc.cu.
+int rt_internal_step_params(const rt_grid_desc* desc, const rt_step_inputs* in, PhysParams* out) {
+    if (!desc || !in || !out) return RT_EINVAL;
+    const rt_grid_desc& d = *desc;
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1 || !(d.dx > 0) || !(d.u_x > 0) || !(d.u_t > 0) || !(d.u_g > 0) ||
+        !(d.theta > 0.0 && d.theta <= 1.0)) {
+        set_detail("invalid descriptor");
+        return RT_EINVAL;
+    }
+    for (int k = 0; k < 3; ++k)
+        if (d.bc[k] != RT_BC_PERIODIC && d.bc[k] != RT_BC_WALL) {
+            set_detail("unknown boundary type on axis %d", k);
+            return RT_EINVAL;
+        }
+    int rc = validate_inputs(nullptr, in);
+    if (rc) return rc;
+    const Grey grey = grey_constants(d.spectrum, d.T_B);
+    const double u_d = d.u_g / (d.u_x * d.u_x * d.u_x), u_v = d.u_x / d.u_t;
+    const double u_E = u_d * u_v * u_v, u_n = u_d / kMH;
+    PhysParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.nx = d.nx;
+    P.ny = d.ny;
+    P.nz = d.nz;
+    for (int k = 0; k < 3; ++k) P.per[k] = d.bc[k] == RT_BC_PERIODIC;
+    P.dx = d.dx;
+    P.theta = d.theta;
+    P.c = kC * d.u_t / d.u_x;
+    P.kE = grey.sigma_E * u_n * d.u_x;
+    P.kG = kC * grey.sigma_G * u_E * d.u_t;
+    P.kA = d.u_t * u_n;
+    P.kH = kC * u_n * (grey.sigma_E - kHnu0 * grey.sigma_G) * d.u_t;
+    P.kC = d.u_t / u_E;
+    P.kT = (kGamma - 1.0) * u_v * u_v * kMH / kKB;
+    P.un = u_n;
+    P.E_min = (d.E_min > 0 ? d.E_min : 1e-35) / u_E;
+    P.E_floor = P.E_min;
+    P.e_floor = kKB * 1.0 / ((kGamma - 1.0) * kMH) / (u_v * u_v);
+    P.T_iso = d.T_iso;
+    P.D_const = d.D_const * d.u_t / (d.u_x * d.u_x);
+    P.src_scale = grey.eps_src * d.u_t / (d.u_x * d.u_x * d.u_x * u_E * d.dx * d.dx * d.dx);
+    P.alpha_const = kAlphaB;
+    P.isothermal = d.isothermal;
+    P.recomb = d.recomb;
+    P.cooling = d.cooling;
+    P.limiter = d.limiter;
+    P.a = in->a;
+    P.a3 = in->a * in->a * in->a;
+    P.H = in->adot / in->a;
+    P.dt = in->dt;
+    P.adx = in->a * d.dx;
+    P.wscale = in->dt * d.theta / (P.adx * P.adx);
+    const double x = 2.0 * P.H * in->dt;
+    P.phi_e = in->dt * (std::fabs(x) < 1e-8 ? 1.0 - 0.5 * x + x * x / 6.0 : -std::expm1(-x) / x);
+    P.local_tol = std::max(1e-14, 1e-3 * d.newton_tol);
+    *out = P;
+    return RT_OK;
+}
+
+const char* rt_internal_set_detail(const char* msg) {
+    set_detail("%s", msg);
+    return g_detail;
+}
