@@ -49,6 +49,14 @@ def workload(n):
                                 box_mpc=14.4 * n / 256, ndot_total=1e52 * (n / 256) ** 3)
 
 
+# FP64 flops per cell of one newton_assemble launch on this workload (mean over the five
+# launches of one step at 128^3: 2 x DFMA + DADD + DMUL thread instructions counted by ncu,
+# see profiles/k_assemble_reionization128.md); the kernel is FP64-ALU bound
+ASSEMBLE_FP64_FLOPS_PER_CELL = 1929.0
+# FP64 peak from unit counts and clock: 2 FP64 FMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
+FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.07
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -313,15 +321,28 @@ def main():
     prof = res["prof"] or {}
     dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
     roof = None
+    cells = args.size**3
+    hbm_peak = (peaks or {}).get("hbm_gbs", 6800.0)
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
+
+    def hbm_roof(name, v):
+        ms = v["ms"] / v["launches"]
+        ach = v["bytes"] / v["launches"] / (ms * 1e-3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": None, "peak_source": peak_src, "share_of_step": v["ms"] / res["ms"]}
+
     if dom is not None:
-        per_launch_ms = dom["ms"] / dom["launches"]
-        per_launch_bytes = dom["bytes"] / dom["launches"]
-        achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
-        peak = (peaks or {}).get("hbm_gbs", 6800.0)
-        roof = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s",
-                "share_of_step": dom["ms"] / res["ms"]}
+        if dom_name == "newton_assemble":
+            ms = dom["ms"] / dom["launches"]
+            ach = ASSEMBLE_FP64_FLOPS_PER_CELL * cells / (ms * 1e-3) / 1e12
+            roof = {"kernel": dom_name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3,
+                    "unit": "TFLOP/s", "frac": ach / (FP64_PEAK_GFLOPS / 1e3), "traffic": None,
+                    "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (own probe: 1.19 TFLOP/s)",
+                    "flops_per_cell": ASSEMBLE_FP64_FLOPS_PER_CELL, "share_of_step": dom["ms"] / res["ms"]}
+        else:
+            roof = hbm_roof(dom_name, dom)
+    smooth = prof.get("mg_rbgs")
+    roof_mg = hbm_roof("mg_rbgs", smooth) if smooth else None
     kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                    "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None,
                    "share": v["ms"] / res["ms"]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
@@ -338,6 +359,7 @@ def main():
         "linear_iters": [x["linear_iters"] for x in res["stats"]],
         "fp64": res["fp64"],
         "roofline": roof,
+        "roofline_vcycle_smoother": roof_mg,
         "kernels": kernels,
         "gpu_launches": launches,
         "clocks": res["clocks"],

@@ -130,6 +130,7 @@ struct rt_grid {
     // Newton iterates (current / trial) and the reduced system
     double *Ec, *nc, *ecc, *Et, *nt, *ect;
     double *step, *diag, *rhs, *wE;
+    double *Xec, *Xnc, *Xet, *Xnt;   // local-elimination sensitivities (current / trial)
     // CG vectors
     double *x, *r, *z, *p, *q;
     // multigrid
@@ -514,7 +515,8 @@ void rt_destroy_grid(rt_grid* g) {
     if (!g) return;
     cudaSetDevice(g->desc.device);
     double* bufs[] = {g->E0, g->n0, g->src, g->bE, g->wx, g->wy, g->wz, g->Ec, g->nc, g->ecc, g->Et, g->nt, g->ect,
-                      g->step, g->diag, g->rhs, g->wE, g->x, g->r, g->z, g->p, g->q, g->partials, g->dots, g->scal};
+                      g->step, g->diag, g->rhs, g->wE, g->x, g->r, g->z, g->p, g->q, g->partials, g->dots, g->scal,
+                      g->Xec, g->Xnc, g->Xet, g->Xnt};
     for (double* b : bufs) cudaFree(b);
     cudaFree(g->wxf);
     cudaFree(g->wyf);
@@ -621,6 +623,12 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out) {
     double** fp64[] = {&g->E0, &g->n0, &g->src, &g->bE, &g->wx, &g->wy, &g->wz, &g->Ec, &g->nc, &g->ecc, &g->Et,
                        &g->nt, &g->ect, &g->step, &g->diag, &g->rhs, &g->wE, &g->x, &g->r, &g->z, &g->p, &g->q};
     for (double** b : fp64) *b = dalloc<double>(n, ok);
+    if (!d.isothermal) {
+        g->Xec = dalloc<double>(n, ok);
+        g->Xnc = dalloc<double>(n, ok);
+        g->Xet = dalloc<double>(n, ok);
+        g->Xnt = dalloc<double>(n, ok);
+    }
     g->partials = dalloc<double>(RT_RED_SLOTS * RT_MAX_PARTIALS, ok);
     g->dots = dalloc<double>(16, ok);
     g->scal = dalloc<double>(16, ok);
@@ -710,11 +718,15 @@ int rt_implicit_step(rt_grid* g, const rt_step_inputs* in, rt_state* io, rt_step
         A.diag = g->diag;
         A.rhs = g->rhs;
         A.wE = g->wE;
+        A.Xe_cur = have_cur ? g->Xec : nullptr;
+        A.Xn_cur = have_cur ? g->Xnc : nullptr;
+        A.Xe_out = g->Xet;
+        A.Xn_out = g->Xnt;
         // algorithmic bytes per cell: E_k, n guess, E^n, n^n, rho, e_h, b_E, src, 3 faces read;
         // trial E, n, e_c, Schur diagonal, right side and norm weight written
         double per = 8.0 * (1 + 1 + 4 + 2 + 3) + 4.0 + 8.0 * 6;
         if (A.step) per += 8.0;
-        if (!P.isothermal) per += 8.0 + (in->vx ? 24.0 : 0.0);
+        if (!P.isothermal) per += 8.0 + (in->vx ? 24.0 : 0.0) + 16.0 + (have_cur ? 16.0 : 0.0);
         int nb = 0;
         run(g, K_ASSEMBLE, (double)n * per, [&] { nb = launch_assemble(P, A, false, s); });
         st.residual_evals++;
@@ -756,6 +768,8 @@ int rt_implicit_step(rt_grid* g, const rt_step_inputs* in, rt_state* io, rt_step
         swap_ptr(g->Ec, g->Et);
         swap_ptr(g->nc, g->nt);
         swap_ptr(g->ecc, g->ect);
+        swap_ptr(g->Xec, g->Xet);
+        swap_ptr(g->Xnc, g->Xnt);
         if (!have_cur) st.norm0 = n_own;
         else st.newton_iters++;
         have_cur = true;

@@ -37,6 +37,8 @@ struct AssembleArgs {
     double lam;
     const double* n_guess;   // local-solve starting values (current iterate)
     const double* ec_guess;
+    const double* Xe_cur;    // optional: d(e_c, n_HI)/dE = -(Xe, Xn) at the current iterate; the
+    const double* Xn_cur;    // local solve then starts from the tangent predictor u - X lam s
     // given-iterate mode (parity entry points): u is taken from here, no local solve
     const double* n_given;
     const double* ec_given;
@@ -61,6 +63,8 @@ struct AssembleArgs {
     double* diag;       // Schur diagonal
     double* rhs;        // Schur right side
     double* wE;         // norm weight of the trial (for the linear solver's residual norm)
+    double* Xe_out;     // optional: X = J_uu^-1 J_uE at the trial (non-isothermal)
+    double* Xn_out;
     double* fE_out;     // optional residual outputs (parity entry points)
     double* fn_out;
     double* fe_out;

@@ -9,9 +9,10 @@
 //      - red-black Gauss-Seidel smoothing;
 //      - fused residual + restriction (average of the 8 children);
 //      - trilinear cell-centred prolongation added to the fine correction;
-//      - coarse operators by averaging: sigma_c = mean of the children's sigma = diag - sum w,
-//        coarse face coupling = sum of the 4 fine face couplings / 16 (what re-discretising the
-//        diffusion term on the doubled cell gives for constant coefficients);
+//      - coarse operators by averaging: sigma_c = geometric mean of the children's
+//        sigma = diag - sum w, coarse face coupling = sum of the 4 fine face couplings / 16
+//        (what re-discretising the diffusion term on the doubled cell gives for constant
+//        coefficients);
 //      - a single-CTA solver that runs the remaining coarse levels in shared memory and finishes
 //        with a dense Cholesky solve (or the exact 1-cell solve) on the coarsest one.
 #include "kernels.cuh"
@@ -329,6 +330,10 @@ __device__ __forceinline__ void coarsen_cell(const Dims& fd, const T* fdiag, con
                                              T* cwy, T* cwz) {
     const long long fsy = fd.nx, fsz = (long long)fd.nx * fd.ny;
     auto fi = [&](int x, int y, int z) { return (long long)z * fsz + (long long)y * fsy + x; };
+    // coarse sigma: geometric mean of the children's sigma.  Around a small ionised bubble
+    // the children mix sigma ~ 1 (transparent) with sigma ~ 1e4 (neutral, optically thick);
+    // an arithmetic mean makes every coarse cell touching neutral gas look opaque and the
+    // bubble's smooth error modes get no coarse correction (measured: more CG iterations)
     T sig = T(0);
     for (int k = 0; k < 2; ++k)
         for (int j = 0; j < 2; ++j)
@@ -338,9 +343,10 @@ __device__ __forceinline__ void coarsen_cell(const Dims& fd, const T* fdiag, con
                 const T wxm = (!fd.per[0] && x == 0) ? T(0) : fwx[fi(dn(x, fd.nx, fd.per[0]), y, z)];
                 const T wym = (!fd.per[1] && y == 0) ? T(0) : fwy[fi(x, dn(y, fd.ny, fd.per[1]), z)];
                 const T wzm = (!fd.per[2] && z == 0) ? T(0) : fwz[fi(x, y, dn(z, fd.nz, fd.per[2]))];
-                sig += fdiag[i] - (fwx[i] + fwy[i] + fwz[i] + wxm + wym + wzm);
+                const T sc = fdiag[i] - (fwx[i] + fwy[i] + fwz[i] + wxm + wym + wzm);
+                sig += log(sc > T(1e-30) ? sc : T(1e-30));
             }
-    sig *= T(0.125);
+    sig = exp(sig * T(0.125));
     // + faces: fine faces leaving the children on the + side
     T ax = T(0), ay = T(0), az = T(0), bx = T(0), by = T(0), bz = T(0);
     for (int a = 0; a < 2; ++a)

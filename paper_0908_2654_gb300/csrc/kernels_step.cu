@@ -161,7 +161,7 @@ __global__ void k_setup(PhysParams P, const double* __restrict__ E0, const doubl
 // Local equations f_e = e_c - S_e, f_n = n - S_n at fixed E: solution, residual and the
 // pieces of the Schur reduction, X = (J_uu^-1 J_uE)_n and Y = (J_uu^-1 f_u)_n.
 struct LocalOut {
-    double ec, n, fe, fn, X, Y;
+    double ec, n, fe, fn, X, Y, Xe;
 };
 
 template <bool ISO, bool GIVEN>
@@ -177,6 +177,7 @@ __device__ __forceinline__ LocalOut local_block(const PhysParams& P, const CellI
         o.fn = o.n - Sn.v;
         o.X = -Sn.d[0];
         o.Y = o.fn;
+        o.Xe = 0.0;
         return o;
     }
     // damped 2x2 Newton: steps are halved until max(|f_e|/e_int, |f_n|/n_H) decreases,
@@ -226,6 +227,7 @@ __device__ __forceinline__ LocalOut local_block(const PhysParams& P, const CellI
     o.fn = fn;
     o.X = (a11 * bn - a21 * be) / det;
     o.Y = (a11 * fn - a21 * fe) / det;
+    o.Xe = (a22 * be - a12 * bn) / det;
     return o;
 }
 
@@ -258,8 +260,14 @@ __global__ void __launch_bounds__(kBlock) k_assemble(PhysParams P, AssembleArgs 
         c.clump = A.clump ? (double)A.clump[i] : 1.0;
         const double se = fmax(c.eh_kin, P.e_floor);
 
-        const double ec_in = GIVEN ? A.ec_given[i] : (A.ec_guess ? A.ec_guess[i] : 0.0);
-        const double n_in = GIVEN ? A.n_given[i] : A.n_guess[i];
+        double ec_in = GIVEN ? A.ec_given[i] : (A.ec_guess ? A.ec_guess[i] : 0.0);
+        double n_in = GIVEN ? A.n_given[i] : A.n_guess[i];
+        if (!GIVEN && !ISO && A.Xe_cur && st) {
+            // tangent predictor: u(E + dE) ~ u(E) - X dE, from the elimination at the current iterate
+            const double dE = lam * st[i];
+            ec_in = fmax(ec_in - A.Xe_cur[i] * dE, -0.999 * c.eh_kin);
+            n_in = fmin(fmax(n_in - A.Xn_cur[i] * dE, 1e-300), c.rho);
+        }
         const LocalOut L = local_block<ISO, GIVEN>(P, c, E, ec_in, n_in, se);
 
         const double kap = P.kE * L.n / P.a3;
@@ -286,6 +294,10 @@ __global__ void __launch_bounds__(kBlock) k_assemble(PhysParams P, AssembleArgs 
         if (A.fE_out) A.fE_out[i] = fE;
         if (A.fn_out) A.fn_out[i] = L.fn;
         if (A.fe_out) A.fe_out[i] = L.fe;
+        if (A.Xe_out) {
+            A.Xe_out[i] = L.Xe;
+            A.Xn_out[i] = L.X;
+        }
     }
     block_sums<3>(acc, A.partials);
 }

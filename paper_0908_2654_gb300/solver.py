@@ -26,7 +26,7 @@ class Solver:
     """
 
     def __init__(self, w, precision="mixed", newton_tol=1e-8, lin_rtol=1e-3, max_newton=40, max_lin=200,
-                 nu=(2, 2), theta=None, device=0, stream=None, limiter="lagged", D_const=0.0, E_min=1e-35):
+                 nu=(4, 4), theta=None, device=0, stream=None, limiter="lagged", D_const=0.0, E_min=1e-35):
         self.w = w
         self.dev = torch.device("cuda", device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.dev)
