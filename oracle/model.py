@@ -176,8 +176,9 @@ def opacity(st, nHI):
 
 def emissivity(st):
     """4 pi eta per cell: point sources inject Ndot eps_src into the comoving cell volume."""
-    src = np.zeros(st.N)
-    np.add.at(src, np.asarray(st.src_index, dtype=np.int64), np.asarray(st.src_ndot) * st.eps_src / st.dx**3)
+    ndot = np.asarray(st.src_ndot)
+    src = np.zeros(st.N, dtype=np.result_type(ndot, float))
+    np.add.at(src, np.asarray(st.src_index, dtype=np.int64), ndot * st.eps_src / st.dx**3)
     return src.reshape(st.shape)
 
 

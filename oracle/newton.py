@@ -265,12 +265,12 @@ def solve_step(st, tol=1e-11, maxit=60, freeze=False, linear="auto", U0=None, ve
         S = linear_solve(J, -f.ravel(), linear).reshape(U.shape)
         sE = S[2]
         lam = 1.0
-        for _ in range(60):
+        for _ in range(40):
             Ut = U.copy()
             Ut[2] = U[2] + lam * sE
             Ut = local_solve(st, Ut)
             nt = M.rms_norm(w, M.residual(st, Ut, bE))
-            if nt <= (1.0 - 1e-4 * lam) * nrm:
+            if nt <= (1.0 - 1e-4 * lam) * nrm and nt < nrm:
                 break
             lam *= 0.5
         else:
