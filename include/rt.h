@@ -190,7 +190,18 @@ int rt_get_profile(rt_grid* g, rt_kernel_profile* out, int max_entries, int* n_e
 int rt_residual_static(const rt_grid_desc* desc, const rt_step_inputs* in, const rt_state* U_n,
                        const rt_state* U, double* f_e, double* f_n, double* f_E);
 
-/* Discrete adjoint of one step (not available in this version: returns RT_EINVAL). */
+/* Discrete adjoint of one step (the step map of Sec. "Algorithm": U^{n+1} is the root of
+ * f(U; X^n, p) = 0 with X^n = (E^n, n_HI^n, e_h^n) the state handed over by the operator split
+ * and X^{n+1} = (E, n_HI, e_h^n + e_c)).  Given lam_np1 = dJ/dX^{n+1} for an objective J, it
+ * solves the transposed Newton system at the converged state with the same Schur reduction and
+ * multigrid-preconditioned CG as the forward step, and returns lam_n = dJ/dX^n through this
+ * step.  The e_c slot of lam_np1 / lam_n holds the adjoint of the gas energy e_h.
+ * U_n: the step's start state (E^n, n_HI^n; e_c unused); U_np1: its converged result
+ * (rt_implicit_step output); in: the same inputs as that step (e_h = e_h^n).
+ * g_ndot (nsrc values, may be NULL) and g_clump (nx*ny*nz FP32 values, may be NULL) are
+ * ACCUMULATED: += dJ/dNdot_s [1/(photons/s)] and += dJ/dC of this step.  lam_n may alias
+ * lam_np1.  All arrays are device arrays in the normalised units of the state.
+ * Errors: RT_EINVAL, RT_ELINEAR, RT_ENONFINITE, RT_ECUDA. */
 int rt_adjoint_step(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U_np1,
                     const rt_state* lam_np1, rt_state* lam_n, double* g_ndot, float* g_clump);
 

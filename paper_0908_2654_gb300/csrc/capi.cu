@@ -927,9 +927,61 @@ int rt_fold_energy(rt_grid* g, double* e_h, const double* e_c) {
 
 int rt_adjoint_step(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U_np1,
                     const rt_state* lam_np1, rt_state* lam_n, double* g_ndot, float* g_clump) {
-    (void)g; (void)in; (void)U_n; (void)U_np1; (void)lam_np1; (void)lam_n; (void)g_ndot; (void)g_clump;
-    set_detail("the adjoint step is not available in this version");
-    return RT_EINVAL;
+    if (!g || !U_n || !U_np1 || !lam_np1 || !lam_n || !U_n->E || !U_n->n_HI || !U_np1->E || !U_np1->n_HI ||
+        !U_np1->e_c || !lam_np1->E || !lam_np1->n_HI || !lam_np1->e_c || !lam_n->E || !lam_n->n_HI || !lam_n->e_c) {
+        set_detail("null state or adjoint array");
+        return RT_EINVAL;
+    }
+    int rc = validate_inputs(g, in);
+    if (rc) return rc;
+    RT_CUDA(cudaSetDevice(g->desc.device));
+    g->launches = 0;
+    PhysParams P = step_params(g, in);
+    rc = step_setup(g, in, P, U_n->E, U_n->n_HI);
+    if (rc) return rc;
+    cudaStream_t s = g->stream;
+    // forward Schur operator at the converged state (symmetric: also the adjoint operator)
+    AssembleArgs F = base_args(g, in);
+    F.E_cur = U_np1->E;
+    F.n_given = U_np1->n_HI;
+    F.ec_given = U_np1->e_c;
+    F.diag = g->diag;
+    F.rhs = g->rhs;
+    F.wE = g->wE;
+    run(g, K_ASSEMBLE, 0.0, [&] { launch_assemble(P, F, true, s); });
+    AdjointArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.rho = in->rho_b;
+    A.e_h = in->e_h;
+    A.vx = in->vx;
+    A.vy = in->vy;
+    A.vz = in->vz;
+    A.clump = in->clump;
+    A.E0 = g->E0;
+    A.n0 = g->n0;
+    A.E = U_np1->E;
+    A.nHI = U_np1->n_HI;
+    A.ec = U_np1->e_c;
+    A.lam_E_in = lam_np1->E;
+    A.lam_n_in = lam_np1->n_HI;
+    A.lam_eh_in = lam_np1->e_c;
+    A.rhs = g->rhs;
+    run(g, K_ASSEMBLE, 0.0, [&] { launch_adj_rhs(P, A, s); });
+    bind_operator_levels(g);
+    run(g, K_ZERO, 0.0, [&] { launch_zero(g->step, g->n, s); });
+    int its = 0;
+    rc = pcg(g, g->rhs, g->step, nullptr, std::min(g->desc.lin_rtol, 1e-10), g->desc.max_lin, &its);
+    if (rc) return rc;
+    A.muE = g->step;
+    A.lam_E_out = lam_n->E;
+    A.lam_n_out = lam_n->n_HI;
+    A.lam_eh_out = lam_n->e_c;
+    A.g_clump = g_clump;
+    A.g_ndot = g_ndot;
+    A.src_cell = in->src_cell;
+    run(g, K_ASSEMBLE, 0.0, [&] { launch_adj_back(P, A, g_ndot ? in->nsrc : 0, s); });
+    RT_CUDA(cudaStreamSynchronize(s));
+    return check_launch("adjoint step");
 }
 
 }  // extern "C"

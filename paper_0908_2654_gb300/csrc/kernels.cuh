@@ -72,6 +72,34 @@ struct AssembleArgs {
 };
 int launch_assemble(const PhysParams& P, const AssembleArgs& A, bool given_u, cudaStream_t s);
 
+// ---- discrete adjoint of one step
+struct AdjointArgs {
+    const double* rho;
+    const double* e_h;
+    const double* vx;
+    const double* vy;
+    const double* vz;
+    const float* clump;
+    const double* E0;        // start state
+    const double* n0;
+    const double* E;         // converged end state U = (e_c, n_HI, E)
+    const double* nHI;
+    const double* ec;
+    const double* lam_E_in;  // adjoint of the hand-over state (E, n_HI, e_h)
+    const double* lam_n_in;
+    const double* lam_eh_in;
+    double* rhs;             // reduced adjoint right side
+    const double* muE;       // reduced adjoint solution
+    double* lam_E_out;       // adjoint of the start state
+    double* lam_n_out;
+    double* lam_eh_out;
+    float* g_clump;          // += dJ/dC
+    double* g_ndot;          // += dJ/dNdot
+    const int64_t* src_cell;
+};
+void launch_adj_rhs(const PhysParams& P, const AdjointArgs& A, cudaStream_t s);
+void launch_adj_back(const PhysParams& P, const AdjointArgs& A, int nsrc, cudaStream_t s);
+
 // ---- reductions (deterministic: block partials then one ordered pass)
 void launch_finalize(const double* partials, int nblocks, int nslots, double* out, cudaStream_t s);
 // slots [0, nsum) are summed, slots [nsum, nsum + nmax) are maxima

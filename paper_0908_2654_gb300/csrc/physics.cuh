@@ -97,6 +97,19 @@ RT_HD TFactors<T> t_factors(const T& temp) {
     return f;
 }
 
+// the same solution with the initial value y0 and the coefficients all of type T (used by
+// the adjoint, which differentiates with respect to the step's starting state)
+template <class T>
+RT_HD T riccati_n_full(const T& y0, double nH, const T& A, const T& G, double dt) {
+    T d = sqrt(G * G + 4.0 * nH * (A * G));
+    T den = 2.0 * nH * A + G + d;
+    T yeq = (value(den) > 0.0) ? (2.0 * nH * nH) * A / den : den * 0.0;
+    T u0 = y0 - yeq;
+    T x = d * dt;
+    T q = exp(-x);
+    return yeq + u0 * q / (1.0 - (u0 * A) * (dt * phi1(x)));
+}
+
 // case-B recombination coefficient [cm^3/s], Hui & Gnedin (1997):
 // 2.753e-14 lam^1.5 / (1 + (lam/2.740)^0.407)^2.242
 template <class T>
@@ -164,6 +177,54 @@ RT_HD void local_solutions(const PhysParams& P, const CellIn& c, const T& ec, co
         cool = (P.kC * P.a3 / c.rho) * cooling_volume(tf, nHII, nHIp, nHII, P.a);
     }
     Se = (heat - cool) * P.phi_e;
+}
+
+// local_solutions with the start-of-step values E^n, n_HI^n and the clumping factor C also
+// of type T (their partial derivatives feed the adjoint of the step map)
+template <class T>
+RT_HD void local_solutions_full(const PhysParams& P, const CellIn& c, const T& ec, const T& n, const T& E,
+                                const T& E0, const T& y0, const T& C, T& Se, T& Sn) {
+    T Ebar = spos(P.theta * E + (1.0 - P.theta) * E0, P.E_min);
+    T G = (P.kG / P.a3) * Ebar;
+    T temp;
+    if (P.isothermal) {
+        temp = ec * 0.0 + P.T_iso;
+    } else {
+        temp = (P.kT * c.rho) * (c.eh_kin + ec) / (2.0 * c.rho - n);
+        if (value(temp) < RT_T_FLOOR) temp = temp * 0.0 + RT_T_FLOOR;
+    }
+    const bool need_t = P.recomb != 0 || (!P.isothermal && P.cooling);
+    TFactors<T> tf;
+    if (need_t) tf = t_factors(temp);
+    T alpha = (P.recomb == 0) ? temp * 0.0 + P.alpha_const : alpha_hg97(tf);
+    T A = alpha * (P.kA / P.a3) * C;
+    Sn = riccati_n_full(y0, c.rho, A, G, P.dt);
+    if (P.isothermal) {
+        Se = ec * 0.0;
+        return;
+    }
+    T heat = (P.kH / (P.a3 * c.rho)) * (n * Ebar);
+    T cool = heat * 0.0;
+    if (P.cooling) {
+        const double s = P.un / P.a3;
+        T nHII = (c.rho - n) * s;
+        T nHIp = n * s;
+        cool = (P.kC * P.a3 / c.rho) * cooling_volume(tf, nHII, nHIp, nHII, P.a);
+    }
+    Se = (heat - cool) * P.phi_e;
+}
+
+// Eq. limiter at a face for any scalar type (the adjoint differentiates D with respect to
+// the start-of-step state it is evaluated from)
+template <class T>
+RT_HD T limiter_face_t(const PhysParams& P, const T& Ei, const T& Ej, const T& ki, const T& kj) {
+    if (P.limiter == 1) return Ei * 0.0 + P.D_const;
+    T Ef = spos(0.5 * (Ei + Ej), P.E_min);
+    T dE = Ej - Ei;
+    T R = (value(dE) >= 0.0 ? dE : -dE) / (P.adx * Ef);
+    T kT = 0.5 * (ki + kj);
+    if (value(kT) == 0.0 && value(R) == 0.0) R = R * 0.0 + 1.0 / P.adx;
+    return P.c * (2.0 * kT + R) / ((6.0 * kT + 3.0 * R) * kT + R * R);
 }
 
 // Eq. limiter on a face between cells with energies (Ei, Ej) and proper opacities
