@@ -173,6 +173,11 @@ typedef struct {
 int rt_set_profiling(rt_grid* g, int on);
 int rt_get_profile(rt_grid* g, rt_kernel_profile* out, int max_entries, int* n_entries);
 
+/* Diagnostic: evaluates the library's table-driven FP64 exp (fn 0) or log (fn 1) used by the
+ * rate fits, or the CUDA math library's exp (fn 2) / log (fn 3), on n device values x into y,
+ * on the given stream (NULL = legacy default stream).  Errors: RT_EINVAL, RT_ECUDA. */
+int rt_eval_elementary(int fn, const double* x, double* y, long long n, void* stream);
+
 /* Allocation-free residual.  The paper has no counterpart: this is a service for callers
  * that cannot allocate device memory (an application that owns the whole device memory
  * budget through its own pool, work issued during CUDA stream capture, allocation-free

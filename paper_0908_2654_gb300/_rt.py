@@ -85,7 +85,7 @@ _lib = None
 EXPORTS = ["rt_init_grid", "rt_implicit_step", "rt_residual", "rt_schur_system", "rt_schur_solve",
            "rt_adjoint_step", "rt_fold_energy", "rt_destroy_grid", "rt_error_string",
            "rt_last_error_detail", "rt_grey_constants", "rt_set_profiling", "rt_get_profile",
-           "rt_residual_static"]
+           "rt_residual_static", "rt_eval_elementary"]
 
 
 def lib():
@@ -114,6 +114,7 @@ def lib():
     L.rt_last_error_detail.restype = ctypes.c_char_p
     L.rt_grey_constants.argtypes = [ctypes.c_void_p] + [P(ctypes.c_double)] * 3
     L.rt_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.rt_eval_elementary.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]
     L.rt_residual_static.argtypes = [P(GridDesc), P(StepInputs), P(State), P(State)] + [ctypes.c_void_p] * 3
     L.rt_get_profile.argtypes = [ctypes.c_void_p, P(KernelProfile), ctypes.c_int, P(ctypes.c_int)]
     for name in EXPORTS:

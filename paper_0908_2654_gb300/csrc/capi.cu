@@ -878,6 +878,18 @@ int rt_schur_solve(rt_grid* g, const double* b, double* x, double rtol, int max_
     return check_launch("schur solve");
 }
 
+int rt_eval_elementary(int fn, const double* x, double* y, long long n, void* stream) {
+    if (fn < 0 || fn > 3 || n < 0 || (n > 0 && (!x || !y))) {
+        set_detail("invalid rt_eval_elementary arguments");
+        return RT_EINVAL;
+    }
+    if (n == 0) return RT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_elementary(fn, x, y, n, s);
+    RT_CUDA(cudaStreamSynchronize(s));
+    return check_launch("elementary functions");
+}
+
 int rt_set_profiling(rt_grid* g, int on) {
     if (!g) return RT_EINVAL;
     RT_CUDA(cudaSetDevice(g->desc.device));

@@ -72,6 +72,9 @@ struct AssembleArgs {
 };
 int launch_assemble(const PhysParams& P, const AssembleArgs& A, bool given_u, cudaStream_t s);
 
+// ---- elementary functions (fn 0: table exp, 1: table log, 2: CUDA exp, 3: CUDA log)
+void launch_elementary(int fn, const double* x, double* y, long long n, cudaStream_t s);
+
 // ---- discrete adjoint of one step
 struct AdjointArgs {
     const double* rho;

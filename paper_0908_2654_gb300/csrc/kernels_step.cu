@@ -339,6 +339,13 @@ __global__ void k_finalize_ext(const double* __restrict__ partials, int nblocks,
     }
 }
 
+__global__ void k_elementary(int fn, const double* __restrict__ x, double* __restrict__ y, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        y[i] = fn == 0 ? rt_exp(v) : fn == 1 ? rt_log(v) : fn == 2 ? exp(v) : log(v);
+    }
+}
+
 int grid_for(long long n) {
     long long b = (n + kBlock - 1) / kBlock;
     const long long cap = 152LL * 8;
@@ -383,6 +390,10 @@ int launch_assemble(const PhysParams& P, const AssembleArgs& A, bool given_u, cu
         else k_assemble<false, false><<<g, kBlock, 0, s>>>(P, A);
     }
     return g;
+}
+
+void launch_elementary(int fn, const double* x, double* y, long long n, cudaStream_t s) {
+    k_elementary<<<grid_for(n), kBlock, 0, s>>>(fn, x, y, n);
 }
 
 void launch_finalize(const double* partials, int nblocks, int nslots, double* out, cudaStream_t s) {

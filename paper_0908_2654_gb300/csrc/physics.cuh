@@ -11,7 +11,35 @@
 //    (Hui & Gnedin 1997), collisional excitation and bremsstrahlung (Cen 1992) and
 //    Compton scattering off the CMB.
 #pragma once
+#include <cmath>
+
 #include "dual.cuh"
+#include "fastmath.cuh"
+
+// exp and log of the rate fits: the table-driven versions of fastmath.cuh on the device
+RT_HD double fexp(double x) {
+#ifdef __CUDA_ARCH__
+    return rt_exp(x);
+#else
+    return std::exp(x);
+#endif
+}
+RT_HD double flog(double x) {
+#ifdef __CUDA_ARCH__
+    return rt_log(x);
+#else
+    return std::log(x);
+#endif
+}
+template <int K>
+RT_HD Dual<K> fexp(const Dual<K>& a) {
+    const double e = fexp(a.v);
+    return dchain(a, e, e);
+}
+template <int K>
+RT_HD Dual<K> flog(const Dual<K>& a) {
+    return dchain(a, flog(a.v), 1.0 / a.v);
+}
 
 struct PhysParams {
     // grid
@@ -62,6 +90,14 @@ RT_HD T phi1(const T& x) {
     return -expm1(-x) / x;
 }
 
+// e^-x and phi1(x) = (1 - e^-x)/x from one expm1 (series for phi1 at |x| < 1e-8)
+template <class T>
+RT_HD void decay_factors(const T& x, T& q, T& p1) {
+    const T em = expm1(-x);
+    q = em + 1.0;
+    p1 = (fabs(value(x)) < 1e-8) ? 1.0 - x * 0.5 + x * x * (1.0 / 6.0) : -em / x;
+}
+
 // n(dt) for n' = A (nH - n)^2 - G n, n(0) = y0.
 // The right side is A (n - y_eq)(n - y_2) with y_eq = 2 A nH^2 / (2 A nH + G + d),
 // d = sqrt(G^2 + 4 A G nH) = A (y_2 - y_eq).  u = n - y_eq obeys u' = A u^2 - d u, so
@@ -72,9 +108,9 @@ RT_HD T riccati_n(double y0, double nH, const T& A, const T& G, double dt) {
     T den = 2.0 * nH * A + G + d;
     T yeq = (value(den) > 0.0) ? (2.0 * nH * nH) * A / den : den * 0.0;
     T u0 = y0 - yeq;
-    T x = d * dt;
-    T q = exp(-x);
-    return yeq + u0 * q / (1.0 - (u0 * A) * (dt * phi1(x)));
+    T q, p1;
+    decay_factors(d * dt, q, p1);
+    return yeq + u0 * q / (1.0 - (u0 * A) * (dt * p1));
 }
 
 // Temperature-dependent factors shared by the recombination coefficient and the cooling
@@ -89,7 +125,7 @@ RT_HD TFactors<T> t_factors(const T& temp) {
     TFactors<T> f;
     f.temp = temp;
     f.invT = 1.0 / temp;
-    f.logT = log(temp);
+    f.logT = flog(temp);
     f.sqrtT = sqrt(temp);
     f.lam = (2.0 * RT_T_HI) * f.invT;
     f.loglam = 12.662275226919286 - f.logT;            // log(2 T_HI) - log T, log(315614)
@@ -105,35 +141,69 @@ RT_HD T riccati_n_full(const T& y0, double nH, const T& A, const T& G, double dt
     T den = 2.0 * nH * A + G + d;
     T yeq = (value(den) > 0.0) ? (2.0 * nH * nH) * A / den : den * 0.0;
     T u0 = y0 - yeq;
-    T x = d * dt;
-    T q = exp(-x);
-    return yeq + u0 * q / (1.0 - (u0 * A) * (dt * phi1(x)));
+    T q, p1;
+    decay_factors(d * dt, q, p1);
+    return yeq + u0 * q / (1.0 - (u0 * A) * (dt * p1));
 }
 
 // case-B recombination coefficient [cm^3/s], Hui & Gnedin (1997):
 // 2.753e-14 lam^1.5 / (1 + (lam/2.740)^0.407)^2.242
 template <class T>
 RT_HD T alpha_hg97(const TFactors<T>& f) {
-    T p = exp(0.407 * (f.loglam - 1.0079579203999789));            // (lam / 2.740)^0.407
-    return 2.753e-14 * (f.lam * f.sqrtlam) * exp(-2.242 * log1p(p));
+    T p = fexp(0.407 * (f.loglam - 1.0079579203999789));           // (lam / 2.740)^0.407
+    return 2.753e-14 * (f.lam * f.sqrtlam) * fexp(-2.242 * flog(1.0 + p));
 }
 
-// cooling per unit proper volume [erg cm^-3 s^-1] from proper densities [cm^-3]:
-// case-B recombination (Hui & Gnedin 1997), collisional excitation and bremsstrahlung
-// (Cen 1992), Compton scattering off the CMB
+// cooling per unit proper volume [erg cm^-3 s^-1] is (rf n_HII + ce n_HI + comp) n_e with
+// proper densities [cm^-3] and temperature-only coefficients: rf = case-B recombination
+// (Hui & Gnedin 1997) plus bremsstrahlung (Cen 1992), ce = collisional excitation (Cen 1992),
+// comp = Compton scattering off the CMB (per electron)
 template <class T>
-RT_HD T cooling_volume(const TFactors<T>& f, const T& ne, const T& nHI, const T& nHII, double a) {
-    T q = exp(0.376 * (f.loglam - 0.8109302162163288));            // (lam / 2.250)^0.376
-    T rec = 3.435e-30 * f.temp * exp(1.970 * f.loglam - 3.720 * log1p(q));
-    T ce = 7.5e-19 * exp(-118348.0 * f.invT) / (1.0 + f.sqrtT * 3.1622776601683794e-3);
+struct TRates {
+    T alpha;   // case-B recombination coefficient [cm^3/s]
+    T rf, ce, comp;
+};
+
+template <class T>
+RT_HD TRates<T> t_rates_direct(const PhysParams& P, const T& temp, bool fit_alpha, bool cool) {
+    TRates<T> r;
+    if (!fit_alpha && !cool) {
+        r.alpha = temp * 0.0 + P.alpha_const;
+        return r;
+    }
+    const TFactors<T> f = t_factors(temp);
+    r.alpha = fit_alpha ? alpha_hg97(f) : temp * 0.0 + P.alpha_const;
+    if (!cool) return r;
+    T q = fexp(0.376 * (f.loglam - 0.8109302162163288));           // (lam / 2.250)^0.376
+    T rec = 3.435e-30 * f.temp * fexp(1.970 * f.loglam - 3.720 * flog(1.0 + q));
+    r.ce = 7.5e-19 * fexp(-118348.0 * f.invT) / (1.0 + f.sqrtT * 3.1622776601683794e-3);
     T dl = 5.5 - f.logT * 0.43429448190325176;                     // 5.5 - log10 T
-    T gff = 1.1 + 0.34 * exp(dl * dl * (-1.0 / 3.0));
-    T ff = 1.42e-27 * gff * f.sqrtT;
-    const double Tcmb = 2.725 / a;
+    T gff = 1.1 + 0.34 * fexp(dl * dl * (-1.0 / 3.0));
+    r.rf = rec + 1.42e-27 * gff * f.sqrtT;
+    const double Tcmb = 2.725 / P.a;
     // 4 k_B sigma_T a_rad / (m_e c) in CGS
     const double kcomp = 4.0 * 1.380649e-16 * 6.6524587321e-25 * 7.565723e-15 / (9.1093837015e-28 * 2.99792458e10);
-    T comp = kcomp * (Tcmb * Tcmb) * (Tcmb * Tcmb) * (f.temp - Tcmb);
-    return (rec * nHII + ff * nHII + ce * nHI + comp) * ne;
+    r.comp = kcomp * (Tcmb * Tcmb) * (Tcmb * Tcmb) * (f.temp - Tcmb);
+    return r;
+}
+
+// The rates depend on the cell's state only through T: for a dual-number T they are
+// evaluated with the single derivative d/dT and carried to all partials by the chain rule,
+// which keeps the transcendental-heavy fits off the K-lane arithmetic.
+RT_HD TRates<double> t_rates(const PhysParams& P, double temp, bool fit_alpha, bool cool) {
+    return t_rates_direct(P, temp, fit_alpha, cool);
+}
+template <int K>
+RT_HD TRates<Dual<K>> t_rates(const PhysParams& P, const Dual<K>& temp, bool fit_alpha, bool cool) {
+    const TRates<Dual<1>> r = t_rates_direct(P, dvar<1>(temp.v, 0), fit_alpha, cool);
+    TRates<Dual<K>> o;
+    o.alpha = dchain(temp, r.alpha.v, r.alpha.d[0]);
+    if (cool) {
+        o.rf = dchain(temp, r.rf.v, r.rf.d[0]);
+        o.ce = dchain(temp, r.ce.v, r.ce.d[0]);
+        o.comp = dchain(temp, r.comp.v, r.comp.d[0]);
+    }
+    return o;
 }
 
 // Cell inputs that do not depend on the iterate.
@@ -158,25 +228,23 @@ RT_HD void local_solutions(const PhysParams& P, const CellIn& c, const T& ec, co
         temp = (P.kT * c.rho) * (c.eh_kin + ec) / (2.0 * c.rho - n);
         if (value(temp) < RT_T_FLOOR) temp = temp * 0.0 + RT_T_FLOOR;
     }
-    const bool need_t = P.recomb != 0 || (!P.isothermal && P.cooling);
-    TFactors<T> tf;
-    if (need_t) tf = t_factors(temp);
-    T alpha = (P.recomb == 0) ? temp * 0.0 + P.alpha_const : alpha_hg97(tf);
-    T A = alpha * (P.kA * c.clump / P.a3);
+    const bool cool = !P.isothermal && P.cooling;
+    const TRates<T> rt = t_rates(P, temp, P.recomb != 0, cool);
+    T A = rt.alpha * (P.kA * c.clump / P.a3);
     Sn = riccati_n(c.nHI0, c.rho, A, G, P.dt);
     if (P.isothermal) {
         Se = ec * 0.0;
         return;
     }
     T heat = (P.kH / (P.a3 * c.rho)) * (n * Ebar);
-    T cool = heat * 0.0;
-    if (P.cooling) {
+    T cooling = heat * 0.0;
+    if (cool) {
         const double s = P.un / P.a3;
-        T nHII = (c.rho - n) * s;
+        T nHII = (c.rho - n) * s;                 // = n_e
         T nHIp = n * s;
-        cool = (P.kC * P.a3 / c.rho) * cooling_volume(tf, nHII, nHIp, nHII, P.a);
+        cooling = (P.kC * P.a3 / c.rho) * (((rt.rf * nHII + rt.ce * nHIp) + rt.comp) * nHII);
     }
-    Se = (heat - cool) * P.phi_e;
+    Se = (heat - cooling) * P.phi_e;
 }
 
 // local_solutions with the start-of-step values E^n, n_HI^n and the clumping factor C also
@@ -193,25 +261,23 @@ RT_HD void local_solutions_full(const PhysParams& P, const CellIn& c, const T& e
         temp = (P.kT * c.rho) * (c.eh_kin + ec) / (2.0 * c.rho - n);
         if (value(temp) < RT_T_FLOOR) temp = temp * 0.0 + RT_T_FLOOR;
     }
-    const bool need_t = P.recomb != 0 || (!P.isothermal && P.cooling);
-    TFactors<T> tf;
-    if (need_t) tf = t_factors(temp);
-    T alpha = (P.recomb == 0) ? temp * 0.0 + P.alpha_const : alpha_hg97(tf);
-    T A = alpha * (P.kA / P.a3) * C;
+    const bool cool = !P.isothermal && P.cooling;
+    const TRates<T> rt = t_rates(P, temp, P.recomb != 0, cool);
+    T A = rt.alpha * (P.kA / P.a3) * C;
     Sn = riccati_n_full(y0, c.rho, A, G, P.dt);
     if (P.isothermal) {
         Se = ec * 0.0;
         return;
     }
     T heat = (P.kH / (P.a3 * c.rho)) * (n * Ebar);
-    T cool = heat * 0.0;
-    if (P.cooling) {
+    T cooling = heat * 0.0;
+    if (cool) {
         const double s = P.un / P.a3;
-        T nHII = (c.rho - n) * s;
+        T nHII = (c.rho - n) * s;                 // = n_e
         T nHIp = n * s;
-        cool = (P.kC * P.a3 / c.rho) * cooling_volume(tf, nHII, nHIp, nHII, P.a);
+        cooling = (P.kC * P.a3 / c.rho) * (((rt.rf * nHII + rt.ce * nHIp) + rt.comp) * nHII);
     }
-    Se = (heat - cool) * P.phi_e;
+    Se = (heat - cooling) * P.phi_e;
 }
 
 // Eq. limiter at a face for any scalar type (the adjoint differentiates D with respect to
