@@ -40,6 +40,7 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison run")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--no-advect", action="store_true", help="skip the advection pre-step measurement")
     return p.parse_args()
 
 
@@ -52,7 +53,10 @@ def workload(n):
 # FP64 flops per cell of one newton_assemble launch on this workload (mean over the five
 # launches of one step at 128^3: 2 x DFMA + DADD + DMUL thread instructions counted by ncu,
 # see profiles/k_assemble_reionization128.md); the kernel is FP64-ALU bound
-ASSEMBLE_FP64_FLOPS_PER_CELL = 1929.0
+ASSEMBLE_FP64_FLOPS_PER_CELL = 1591.0
+# FP64 flops per cell of the advection kernel with rho_b (three face Courant numbers and three
+# donor-cell updates of three densities per axis: 3 x (6 + 3 x 4)), counted from the source
+ADVECT_FP64_FLOPS_PER_CELL = 54.0
 # FP64 peak from unit counts and clock: 2 FP64 FMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.07
 
@@ -176,11 +180,31 @@ def run_gpu(args, rank, world, local_rank):
                 "newton_iters": [x["newton_iters"] for x in st64], "linear_iters": [x["linear_iters"] for x in st64],
                 "speedup_mixed_vs_fp64": value / v64}
 
+    advect = None if args.no_advect else run_advect(w, local_rank)
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, w, local_rank, barrier, world)
 
-    return dict(value=value, ms=ms_max, stats=st_mixed, prof=prof, clocks=clocks, fp64=fp64, e2e=e2e, w=w)
+    return dict(value=value, ms=ms_max, stats=st_mixed, prof=prof, clocks=clocks, fp64=fp64, e2e=e2e, w=w,
+                advect=advect)
+
+
+def run_advect(w, local_rank, calls=10, warmup=3):
+    """The advection pre-step (rho_b, n_HI and E by donor cell) on the same field, timed per
+    kernel with CUDA events: {kernel: (launches, ms, algorithmic bytes)}."""
+    from paper_0908_2654_gb300.solver import Solver
+    s = Solver(w, precision="fp64", device=local_rank)
+    for _ in range(warmup):
+        s.advect()
+    s.set_profiling(True)
+    for _ in range(calls):
+        courant = s.advect()
+    prof = s.profile()
+    s.close()
+    out = {k: prof[k] for k in ("advect", "advect_courant") if k in prof}
+    out["courant_max"] = courant
+    return out
 
 
 def run_e2e(args, w, local_rank, barrier, world):
@@ -343,6 +367,17 @@ def main():
             roof = hbm_roof(dom_name, dom)
     smooth = prof.get("mg_rbgs")
     roof_mg = hbm_roof("mg_rbgs", smooth) if smooth else None
+    roof_adv = None
+    if res["advect"] and "advect" in res["advect"]:
+        v = res["advect"]["advect"]
+        ms = v["ms"] / v["launches"]
+        ach = ADVECT_FP64_FLOPS_PER_CELL * cells / (ms * 1e-3) / 1e12
+        roof_adv = {"kernel": "advect", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3,
+                    "unit": "TFLOP/s", "frac": ach / (FP64_PEAK_GFLOPS / 1e3), "traffic": None,
+                    "flops_per_cell": ADVECT_FP64_FLOPS_PER_CELL, "ms_per_call": ms,
+                    "hbm_GBps": v["bytes"] / v["launches"] / (ms * 1e-3) / 1e9,
+                    "courant_max": res["advect"]["courant_max"],
+                    "note": "advection pre-step (rho_b, n_HI, E), timed apart from the implicit step"}
     kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                    "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None,
                    "share": v["ms"] / res["ms"]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
@@ -360,6 +395,7 @@ def main():
         "fp64": res["fp64"],
         "roofline": roof,
         "roofline_vcycle_smoother": roof_mg,
+        "roofline_advect": roof_adv,
         "kernels": kernels,
         "gpu_launches": launches,
         "clocks": res["clocks"],

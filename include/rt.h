@@ -210,6 +210,33 @@ int rt_residual_static(const rt_grid_desc* desc, const rt_step_inputs* in, const
 int rt_adjoint_step(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U_np1,
                     const rt_state* lam_np1, rt_state* lam_n, double* g_ndot, float* g_clump);
 
+/* Advection pre-step: step (iv) of the operator split (Sec. "Operator-Split Hydrodynamics with
+ * Radiative Feedback") carries the densities with the baryon velocity,
+ * d_t q + (1/a) div(q v_b) = 0 for q = n_HI, E (Eqs. enzo-chemical_ionization,
+ * enzo-cons_radiation) and rho_b (Eq. enzo-cons_mass in conservative form), giving the advected
+ * state step (v) starts from.  Scheme: first-order donor cell over in->dt at expansion factor
+ * in->a.  On the face between a cell and its '+' neighbour,
+ * c = (v_cell + v_neighbour)/2 * dt / (a dx) (zero on a wall face); the flux c * q of the cell
+ * the flow leaves moves from one cell to the other.  Moving rho_b with the same fluxes keeps
+ * n_HI <= n_H.  The gas energy e_h belongs to the hydrodynamics (pressure work,
+ * Eq. enzo-cons_energy) and is not touched.
+ * src: E, n_HI read (e_c unused).  dst: E, n_HI written.  rho_src / rho_dst: baryon density in
+ * and out (both NULL to leave it alone).  No written array may overlap another argument array.
+ * in->vx, vy, vz: device velocity components in the units of the state (NULL = 0); only
+ * in->a, in->dt and the velocities are read from in.
+ * courant_max (host pointer, may be NULL) receives the largest per-cell sum of outflow Courant
+ * numbers.  If it exceeds 1 (the donor-cell bound for positivity and stability), nothing is
+ * written and RT_EINVAL is returned.
+ * Errors: RT_EINVAL, RT_ECUDA.  Synchronises the grid's stream. */
+int rt_advect(rt_grid* g, const rt_step_inputs* in, const rt_state* src, rt_state* dst, const double* rho_src,
+              double* rho_dst, double* courant_max);
+
+/* Transpose of rt_advect's linear map (same inputs), for the adjoint of the operator split:
+ * lam_star holds dJ/d(E*, n_HI*) of the advected state, lam receives dJ/d(E, n_HI) before
+ * advection (e_c slots unused).  rho_b is not a differentiated variable (it does not depend on
+ * the source rates or the clumping factor).  Same argument rules and errors as rt_advect. */
+int rt_advect_adjoint(rt_grid* g, const rt_step_inputs* in, const rt_state* lam_star, rt_state* lam);
+
 void rt_destroy_grid(rt_grid* g);
 const char* rt_error_string(int code);
 const char* rt_last_error_detail(void);

@@ -14,10 +14,17 @@ steps (tiny grids only).  Parameters p: the photon rates Ndot_s of the sources a
 per-cell clumping factor C.  Objective: the volume-weighted ionised fraction
 1 - mean(n_HI / n_H) of the final state.
 
+With ``advect=True`` every step is preceded by the advection pre-step of n_HI and E
+(``oracle.advection``, step (iv)), a linear map M: the implicit step starts from (M E, M n_HI,
+e_h) with density M rho_b, and the adjoint of the pre-advection state is M^T applied to the
+adjoint of the advected one (rho_b does not depend on the parameters, so it needs no adjoint;
+the objective uses the final density).
+
 Pinned in tests against central finite differences of the whole forward run.
 """
 import numpy as np
 
+from . import advection as ADV
 from . import constants as K
 from . import driver
 from . import model as M
@@ -50,33 +57,43 @@ def _residual_of(st, U, X=None, ndot=None, clump=None):
     return M.residual(s2, U).ravel()
 
 
-def forward(w, ndot, clump, nsteps, tol=1e-11):
-    """Run nsteps oracle steps; returns (J, checkpoints) with checkpoints[n] = (X^n, U^n, step)."""
+def _advect_args(w, run):
+    a, _ = driver.expansion(w, run.t + 0.5 * run.dt)
+    return w["v"], a, run.dt, w["dx"], w["periodic"]
+
+
+def forward(w, ndot, clump, nsteps, tol=1e-11, advect=False):
+    """Run nsteps oracle steps; returns (J, checkpoints) with checkpoints[n] = (X^n, U^n, step,
+    advection arguments or None), X^n the state the implicit step starts from."""
     run = driver.Run(w)
     X = (run.E.copy(), run.nHI.copy(), run.e_h.copy())
     ckpt = []
     for _ in range(nsteps):
+        adv = _advect_args(w, run) if advect else None
+        if adv:
+            X = (ADV.advect(X[0], *adv), ADV.advect(X[1], *adv), X[2])
+            run.rho_b = ADV.advect(run.rho_b, *adv)
         st = _step_from(run, X, ndot, clump)
         U, _ = N.solve_step(st, tol=tol)
-        ckpt.append((X, U, st))
+        ckpt.append((X, U, st, adv))
         run.t += run.dt
         X = (U[2].copy(), U[1].copy(), X[2] + U[0])
-    return ionised_fraction(X[1], w["rho_b"] / K.M_H), ckpt
+    return ionised_fraction(X[1], run.rho_b / K.M_H), ckpt
 
 
-def gradient(w, ndot, clump, nsteps, tol=1e-11, h=1e-30):
+def gradient(w, ndot, clump, nsteps, tol=1e-11, h=1e-30, advect=False):
     """(J, dJ/dNdot, dJ/dC) by the dense discrete adjoint."""
-    Jval, ckpt = forward(w, ndot, clump, nsteps, tol)
+    Jval, ckpt = forward(w, ndot, clump, nsteps, tol, advect)
     shape = (w["nz"], w["ny"], w["nx"])
     Nc = int(np.prod(shape))
-    nH = w["rho_b"] / K.M_H
+    nH = ckpt[-1][2].rho_b / K.M_H               # final density
     # lambda of the final carried state (E, nHI, e_h)
     lam_E = np.zeros(Nc)
     lam_n = (-1.0 / (Nc * nH)).ravel()
     lam_eh = np.zeros(Nc)
     g_ndot = np.zeros(len(ndot))
     g_clump = np.zeros(Nc)
-    for X, U, st in reversed(ckpt):
+    for X, U, st, adv in reversed(ckpt):
         Uc = np.asarray(U, float)
         JU = N.jacobian(st, Uc).toarray()
         lam_U = np.concatenate([lam_eh, lam_n, lam_E])
@@ -94,6 +111,9 @@ def gradient(w, ndot, clump, nsteps, tol=1e-11, h=1e-30):
         lam_E = lamX[:Nc]
         lam_n = lamX[Nc:2 * Nc]
         lam_eh = lamX[2 * Nc:] + lam_eh          # e_h^{n+1} = e_h^n + e_c passes lambda_eh through
+        if adv:                                  # through the advection pre-step: M^T
+            lam_E = ADV.advect_adjoint(lam_E.reshape(shape), *adv).ravel()
+            lam_n = ADV.advect_adjoint(lam_n.reshape(shape), *adv).ravel()
         for s in range(len(ndot)):
             nd = np.array(ndot, complex)
             hs = h * abs(ndot[s])

@@ -6,8 +6,10 @@ carries the chemical number densities and the radiation energy density,
     d_t n_i + (1/a) div(n_i v_b) = 0,      d_t E + (1/a) div(E v_b) = 0
 
 (Eqs. enzo-chemical_ionization and enzo-cons_radiation), giving the advected (n_i^*, E^*) from
-which step (v) starts.  The paper hands this to the hydrodynamics code (PPM); here it is the
-first-order donor-cell (upwind) finite-volume scheme, written out plainly:
+which step (v) starts.  The baryon density moves with the same velocity (Eq. enzo-cons_mass,
+here in its conservative form) and is transported with the same fluxes, so that n_HI / n_H stays
+a convex combination of neighbouring fractions.  The paper hands this to the hydrodynamics code
+(PPM); here it is the first-order donor-cell (upwind) finite-volume scheme, written out plainly:
 
   * the velocity on a face is the mean of the two cells' components normal to it;
   * the face Courant number is c_f = v_f dt / (a dx) (dx comoving, a the expansion factor);

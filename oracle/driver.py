@@ -54,6 +54,7 @@ class Run:
         self.grey = S.grey_constants(w["spectrum"], w.get("T_B", 1e5))
         self.E = np.array(w["E"], float)
         self.nHI = np.array(w["nHI"], float)
+        self.rho_b = np.array(w["rho_b"], float)
         self.e_h = energy_from_temperature(w["T0"], w["rho_b"], self.nHI, w["v"])
         self.t, self.dt = time_grid(w)
         self.step_index = 0
@@ -64,7 +65,7 @@ class Run:
             a, adot = expansion(w, self.t + 0.5 * self.dt)
         return M.Step(
             nx=w["nx"], ny=w["ny"], nz=w["nz"], dx=w["dx"], periodic=w["periodic"],
-            rho_b=w["rho_b"], e_h=self.e_h, v=w["v"], clump=np.asarray(w["clump"], float),
+            rho_b=self.rho_b, e_h=self.e_h, v=w["v"], clump=np.asarray(w["clump"], float),
             E_n=self.E, nHI_n=self.nHI, a=a, adot=adot, dt=self.dt if dt is None else dt,
             src_index=w["src_index"], src_ndot=w["src_ndot"],
             theta=self.theta, isothermal=w["isothermal"], T_iso=w["T_iso"], recomb=w["recomb"],

@@ -85,7 +85,7 @@ _lib = None
 EXPORTS = ["rt_init_grid", "rt_implicit_step", "rt_residual", "rt_schur_system", "rt_schur_solve",
            "rt_adjoint_step", "rt_fold_energy", "rt_destroy_grid", "rt_error_string",
            "rt_last_error_detail", "rt_grey_constants", "rt_set_profiling", "rt_get_profile",
-           "rt_residual_static", "rt_eval_elementary"]
+           "rt_residual_static", "rt_eval_elementary", "rt_advect", "rt_advect_adjoint"]
 
 
 def lib():
@@ -106,6 +106,9 @@ def lib():
     L.rt_adjoint_step.argtypes = [ctypes.c_void_p, P(StepInputs), P(State), P(State), P(State), P(State),
                                   ctypes.c_void_p, ctypes.c_void_p]
     L.rt_fold_energy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.rt_advect.argtypes = [ctypes.c_void_p, P(StepInputs), P(State), P(State), ctypes.c_void_p, ctypes.c_void_p,
+                            P(ctypes.c_double)]
+    L.rt_advect_adjoint.argtypes = [ctypes.c_void_p, P(StepInputs), P(State), P(State)]
     L.rt_destroy_grid.argtypes = [ctypes.c_void_p]
     L.rt_destroy_grid.restype = None
     L.rt_error_string.argtypes = [ctypes.c_int]

@@ -175,12 +175,14 @@ int check_launch(const char* what) {
 
 enum KClass {
     K_ZERO, K_SOURCES, K_FACES, K_SETUP, K_ASSEMBLE, K_FINALIZE, K_SPMV, K_RESNORM, K_CG_UPDATE, K_DOT2, K_P_UPDATE,
-    K_SCALARS, K_COPY, K_CAST, K_MG_DIAG, K_COARSEN, K_RBGS, K_RESTRICT, K_PROLONG, K_TAIL, K_ADD, K_NCLASS
+    K_SCALARS, K_COPY, K_CAST, K_MG_DIAG, K_COARSEN, K_RBGS, K_RESTRICT, K_PROLONG, K_TAIL, K_ADD, K_ADVECT,
+    K_ADVECT_CHECK, K_NCLASS
 };
 const char* kClassName[K_NCLASS] = {"zero", "scatter_sources", "faces", "setup", "newton_assemble", "finalize",
                                     "cg_spmv_dot", "cg_residual", "cg_update_xr", "cg_dot2", "cg_p_update",
                                     "cg_scalars", "copy", "cast", "mg_diag", "mg_coarsen", "mg_rbgs",
-                                    "mg_resid_restrict", "mg_prolong_add", "mg_coarse_cta", "add"};
+                                    "mg_resid_restrict", "mg_prolong_add", "mg_coarse_cta", "add", "advect",
+                                    "advect_courant"};
 
 // Launch f() as kernel class cls moving `bytes` algorithmic bytes; brackets it with events
 // when profiling is on.
@@ -482,6 +484,73 @@ AssembleArgs base_args(rt_grid* g, const rt_step_inputs* in) {
     A.wz = g->wz;
     A.partials = g->partials;
     return A;
+}
+
+// Donor-cell advection of (E, n_HI) (or the transposed map on their adjoints): checks the
+// Courant bound first, so nothing is written when it fails.
+int advect_call(rt_grid* g, const rt_step_inputs* in, const rt_state* src, rt_state* dst, const double* rho_src,
+                double* rho_dst, double* courant_max, bool transpose) {
+    if (!g || !in || !src || !dst || !src->E || !src->n_HI || !dst->E || !dst->n_HI || (!rho_src != !rho_dst)) {
+        set_detail("null grid, inputs or state array (rho_src and rho_dst must be both set or both NULL)");
+        return RT_EINVAL;
+    }
+    const long long n = g->n;
+    auto overlaps = [n](const double* a, const double* b) { return a && b && a < b + n && b < a + n; };
+    const double* reads[3] = {src->E, src->n_HI, rho_src};
+    const double* writes[3] = {dst->E, dst->n_HI, rho_dst};
+    for (int w = 0; w < 3; ++w) {
+        for (int r = 0; r < 3; ++r)
+            if (overlaps(writes[w], reads[r])) {
+                set_detail("advection source and destination arrays overlap");
+                return RT_EINVAL;
+            }
+        for (int w2 = w + 1; w2 < 3; ++w2)
+            if (overlaps(writes[w], writes[w2])) {
+                set_detail("advection destination arrays overlap");
+                return RT_EINVAL;
+            }
+    }
+    if (!(in->a > 0.0) || !(in->dt >= 0.0) || !std::isfinite(in->a) || !std::isfinite(in->dt)) {
+        set_detail("invalid expansion factor or time step (a = %g, dt = %g)", in->a, in->dt);
+        return RT_EINVAL;
+    }
+    RT_CUDA(cudaSetDevice(g->desc.device));
+    AdvectArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.nx = g->desc.nx;
+    A.ny = g->desc.ny;
+    A.nz = g->desc.nz;
+    for (int d = 0; d < 3; ++d) A.per[d] = g->desc.bc[d] == RT_BC_PERIODIC;
+    A.k = in->dt / (in->a * g->desc.dx);
+    A.v[0] = in->vx;
+    A.v[1] = in->vy;
+    A.v[2] = in->vz;
+    A.qE = src->E;
+    A.qn = src->n_HI;
+    A.oE = dst->E;
+    A.on = dst->n_HI;
+    A.qr = rho_src;
+    A.orh = rho_dst;
+    A.partials = g->partials;
+    const double N = (double)n;
+    const int nv = (in->vx != nullptr) + (in->vy != nullptr) + (in->vz != nullptr);
+    int nb = 0;
+    run(g, K_ADVECT_CHECK, N * 8.0 * nv, [&] { nb = launch_advect_courant(A, g->stream); });
+    double cmax = 0.0;
+    int rc = read_scalars(g, nb, 0, &cmax, 1);
+    if (rc) return rc;
+    if (courant_max) *courant_max = cmax;
+    if (!(cmax <= 1.0)) {
+        set_detail("advection Courant number %g exceeds 1", cmax);
+        return RT_EINVAL;
+    }
+    run(g, K_ADVECT, N * 8.0 * ((rho_src ? 6 : 4) + nv), [&] { launch_advect(A, transpose, g->stream); });
+    if (g->prof_on) {
+        RT_CUDA(cudaStreamSynchronize(g->stream));
+        harvest(g);
+    }
+    RT_CUDA(cudaStreamSynchronize(g->stream));
+    return check_launch(transpose ? "advection adjoint" : "advection");
 }
 
 template <class T>
@@ -935,6 +1004,15 @@ int rt_fold_energy(rt_grid* g, double* e_h, const double* e_c) {
     }
     RT_CUDA(cudaStreamSynchronize(g->stream));
     return check_launch("fold energy");
+}
+
+int rt_advect(rt_grid* g, const rt_step_inputs* in, const rt_state* src, rt_state* dst, const double* rho_src,
+              double* rho_dst, double* courant_max) {
+    return advect_call(g, in, src, dst, rho_src, rho_dst, courant_max, false);
+}
+
+int rt_advect_adjoint(rt_grid* g, const rt_step_inputs* in, const rt_state* lam_star, rt_state* lam) {
+    return advect_call(g, in, lam_star, lam, nullptr, nullptr, nullptr, true);
 }
 
 int rt_adjoint_step(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U_np1,

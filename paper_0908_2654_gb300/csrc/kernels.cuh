@@ -72,6 +72,23 @@ struct AssembleArgs {
 };
 int launch_assemble(const PhysParams& P, const AssembleArgs& A, bool given_u, cudaStream_t s);
 
+// ---- advection pre-step (donor cell) and its transpose
+struct AdvectArgs {
+    int nx, ny, nz;
+    int per[3];
+    double k;              // dt / (a dx)
+    const double* v[3];    // velocity components (null: zero)
+    const double* qE;      // forward: E, n_HI; transpose: their adjoints after advection
+    const double* qn;
+    double* oE;
+    double* on;
+    const double* qr;      // optional third density moved by the forward map (rho_b), or null
+    double* orh;
+    double* partials;      // Courant check: one block maximum per block
+};
+int launch_advect_courant(const AdvectArgs& A, cudaStream_t s);   // returns the number of blocks
+void launch_advect(const AdvectArgs& A, bool transpose, cudaStream_t s);
+
 // ---- elementary functions (fn 0: table exp, 1: table log, 2: CUDA exp, 3: CUDA log)
 void launch_elementary(int fn, const double* x, double* y, long long n, cudaStream_t s);
 

@@ -23,10 +23,13 @@ class Solver:
 
     w: workload dict (see ``workloads``), fields in CGS comoving units.
     precision: "fp64" (FP64 multigrid) or "mixed" (FP32 multigrid inside FP64 Newton/CG).
+    advect: run the advection pre-step (step (iv) for rho_b, n_HI and E) before every implicit
+    step.
     """
 
     def __init__(self, w, precision="mixed", newton_tol=1e-8, lin_rtol=1e-3, max_newton=40, max_lin=200,
-                 nu=(4, 4), theta=None, device=0, stream=None, limiter="lagged", D_const=0.0, E_min=1e-35):
+                 nu=(4, 4), theta=None, device=0, stream=None, limiter="lagged", D_const=0.0, E_min=1e-35,
+                 advect=False):
         self.w = w
         self.dev = torch.device("cuda", device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.dev)
@@ -88,6 +91,8 @@ class Solver:
             self.t = self.cosmo.t_of_z(w["z0"])
             self.dt = ((self.cosmo.t_of_z(w["z_end"]) - self.t) / w["nsteps"]) if "z_end" in w else w["dt"]
         self.stats = []
+        self.advection = bool(advect)
+        self._adv = None
 
     # ----------------------------------------------------------------- inputs
     def expansion(self, t):
@@ -120,9 +125,12 @@ class Solver:
         return st
 
     # ------------------------------------------------------------------- steps
-    def step(self, fold=True):
-        """One implicit step (v) in place, then e_h += e_c; returns the step statistics."""
+    def step(self, fold=True, advect=None):
+        """One implicit step (v) in place (after the advection pre-step if ``advect``, default
+        the solver's setting), then e_h += e_c; returns the step statistics."""
         L = _rt.lib()
+        if (self.advection if advect is None else advect) and self.has_v:
+            self.advect()
         stats = _rt.StepStats()
         inp = self.inputs()
         st = self.state()
@@ -136,6 +144,19 @@ class Solver:
         self.t += self.dt
         self.stats.append(stats.as_dict())
         return self.stats[-1]
+
+    def advect(self):
+        """Advection pre-step (step (iv) for rho_b, n_HI and E, donor cell) over this step's
+        dt, in place; returns the largest Courant number."""
+        if self._adv is None:
+            self._adv = tuple(torch.empty_like(self.E) for _ in range(3))
+        inp = self.inputs()
+        c = ctypes.c_double()
+        src, dst = self.state(), self.state(self._adv[0], self._adv[1])
+        _rt.check(_rt.lib().rt_advect(self.handle, ctypes.byref(inp), ctypes.byref(src), ctypes.byref(dst),
+                                      _rt.ptr(self.rho), _rt.ptr(self._adv[2]), ctypes.byref(c)), "rt_advect")
+        (self.E, self.nHI, self.rho), self._adv = self._adv, (self.E, self.nHI, self.rho)
+        return c.value
 
     # ---------------------------------------------------------- kernel access
     def to_device(self, a, scale):

@@ -19,7 +19,7 @@ def _grad(w, nsteps, **opt):
     clump = torch.tensor(np.asarray(w["clump"], np.float32), requires_grad=True)
     J = ionized_fraction(ndot, clump, w, nsteps, **opt)
     J.backward()
-    return float(J), ndot.grad.cpu().numpy(), clump.grad.cpu().numpy()
+    return float(J.detach()), ndot.grad.cpu().numpy(), clump.grad.cpu().numpy()
 
 
 @pytest.mark.parametrize("name,make,nsteps", [
