@@ -114,6 +114,10 @@ typedef struct {
     int line_search_cuts; /* step halvings                                                   */
     double norm0;         /* RMS norm of f at the initial iterate                            */
     double norm;          /* RMS norm of f at the returned state                             */
+    double change_norm;   /* RMS over the 3N unknowns of the step's change, scaled like the
+                             norm (E by max(|E^{n+1}|, |E^n|, E_floor), n_HI by n_H, e_c by
+                             the hydro internal energy): the measure a time-step controller
+                             compares with its tolerance (0 unless the step succeeded)      */
     int kernel_launches;  /* kernels this call launched                                      */
     int nhist;            /* entries used in the histories below                             */
     double hist_norm[RT_STATS_HIST];  /* per evaluation: RMS norm (trial norms use the weights

@@ -63,6 +63,9 @@ class OpenNoLambda:
         eta = optimize.brentq(f, 1e-12, 50.0, xtol=1e-15, rtol=1e-15)
         return Om / (2 * (1 - Om)) * (math.cosh(eta) - 1)
 
+    def t_of_z(self, z):
+        return self.t_of_a(1.0 / (1.0 + z))
+
     def t_of_a(self, a):
         if abs(self.Om - 1.0) < 1e-12:
             return 2.0 / (3.0 * self.H0) * a**1.5

@@ -24,7 +24,11 @@ def energy_from_temperature(T, rho_b, nHI, v):
 
 def cosmology_of(w):
     c = w.get("cosmology")
-    return None if c is None else C.FlatLCDM(**c)
+    if c is None:
+        return None
+    if "q0" in c:                               # the Lambda-free models of Table 1
+        return C.OpenNoLambda(c["q0"], c["h"] * K.H100)
+    return C.FlatLCDM(**c)
 
 
 def time_grid(w):

@@ -59,7 +59,7 @@ class StepStats(ctypes.Structure):
     _fields_ = [
         ("newton_iters", ctypes.c_int), ("residual_evals", ctypes.c_int),
         ("linear_iters", ctypes.c_int), ("line_search_cuts", ctypes.c_int),
-        ("norm0", ctypes.c_double), ("norm", ctypes.c_double),
+        ("norm0", ctypes.c_double), ("norm", ctypes.c_double), ("change_norm", ctypes.c_double),
         ("kernel_launches", ctypes.c_int),
         ("nhist", ctypes.c_int),
         ("hist_norm", ctypes.c_double * 64),

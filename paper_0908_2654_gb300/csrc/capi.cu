@@ -867,6 +867,19 @@ int rt_implicit_step(rt_grid* g, const rt_step_inputs* in, rt_state* io, rt_step
         }
         lam = 1.0;
     }
+    if (rcode == RT_OK) {
+        // the solution change over the step, for time-step control
+        A.E_cur = g->Ec;
+        A.n_guess = g->nc;
+        A.ec_guess = g->ecc;
+        int nb = 0;
+        run(g, K_RESNORM, (double)n * 8.0 * (P.isothermal ? 5 : 7 + (in->vx ? 3 : 0)),
+            [&] { nb = launch_change_norm(P, A, s); });
+        double v = 0.0;
+        rc = read_scalars(g, nb, 1, &v);
+        if (rc) return rc;
+        st.change_norm = std::sqrt(v / (3.0 * (double)n));
+    }
     st.kernel_launches = g->launches;
     if (stats) *stats = st;
     if (g->prof_on) {

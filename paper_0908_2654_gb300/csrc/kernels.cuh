@@ -71,6 +71,8 @@ struct AssembleArgs {
     double* partials;   // RT_RED_SLOTS * nblocks block sums
 };
 int launch_assemble(const PhysParams& P, const AssembleArgs& A, bool given_u, cudaStream_t s);
+// sum of squared scaled changes (E_cur, n_guess, ec_guess) against (E0, n0): one slot per block
+int launch_change_norm(const PhysParams& P, const AssembleArgs& A, cudaStream_t s);
 
 // ---- advection pre-step (donor cell) and its transpose
 struct AdvectArgs {

@@ -302,6 +302,29 @@ __global__ void __launch_bounds__(kBlock) k_assemble(PhysParams P, AssembleArgs 
     block_sums<3>(acc, A.partials);
 }
 
+// Sum over cells of the squared component-scaled change of (e_c, n_HI, E) over the step
+// (e_c^n = 0; E scaled by max(|E^{n+1}|, |E^n|, E_floor), n_HI by n_H, e_c by the hydro
+// state's internal energy): the time-step controller's measure of the solution change.
+__global__ void __launch_bounds__(kBlock) k_change_norm(PhysParams P, AssembleArgs A) {
+    const long long n = (long long)P.nx * P.ny * P.nz;
+    double acc[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double E1 = A.E_cur[i], E0 = A.E0[i];
+        const double dE = (E1 - E0) / fmax(fmax(fabs(E1), fabs(E0)), P.E_floor);
+        const double dn = (A.n_guess[i] - A.n0[i]) / A.rho[i];
+        double de = 0.0;
+        if (!P.isothermal) {
+            double v2 = 0.0;
+            if (A.vx) v2 += A.vx[i] * A.vx[i];
+            if (A.vy) v2 += A.vy[i] * A.vy[i];
+            if (A.vz) v2 += A.vz[i] * A.vz[i];
+            de = A.ec_guess[i] / fmax(A.e_h[i] - 0.5 * v2, P.e_floor);
+        }
+        acc[0] += dE * dE + dn * dn + de * de;
+    }
+    block_sums<1>(acc, A.partials);
+}
+
 __global__ void k_finalize(const double* __restrict__ partials, int nblocks, int nslots, double* out) {
     __shared__ double sh[256];
     for (int k = 0; k < nslots; ++k) {
@@ -389,6 +412,13 @@ int launch_assemble(const PhysParams& P, const AssembleArgs& A, bool given_u, cu
         if (given_u) k_assemble<false, true><<<g, kBlock, 0, s>>>(P, A);
         else k_assemble<false, false><<<g, kBlock, 0, s>>>(P, A);
     }
+    return g;
+}
+
+int launch_change_norm(const PhysParams& P, const AssembleArgs& A, cudaStream_t s) {
+    const long long n = (long long)P.nx * P.ny * P.nz;
+    const int g = grid_for(n);
+    k_change_norm<<<g, kBlock, 0, s>>>(P, A);
     return g;
 }
 

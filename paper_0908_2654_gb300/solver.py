@@ -11,7 +11,7 @@ import numpy as np
 import torch
 
 from . import _rt
-from .cosmology import FlatLCDM
+from .cosmology import from_dict as cosmology_from_dict
 from .units import MYR, Units, specific_energy
 
 _SPECTRA = {"mono": _rt.RT_SPECTRUM_MONO, "blackbody": _rt.RT_SPECTRUM_BLACKBODY}
@@ -84,7 +84,7 @@ class Solver:
         self.e_h = dev(e_h / u.u_v**2)
         # time
         cos = w.get("cosmology")
-        self.cosmo = FlatLCDM(**cos) if cos else None
+        self.cosmo = cosmology_from_dict(cos) if cos else None
         if self.cosmo is None:
             self.t, self.dt = 0.0, w["dt"]
         else:
@@ -93,6 +93,7 @@ class Solver:
         self.stats = []
         self.advection = bool(advect)
         self._adv = None
+        self.courant = None
 
     # ----------------------------------------------------------------- inputs
     def expansion(self, t):
@@ -127,36 +128,89 @@ class Solver:
     # ------------------------------------------------------------------- steps
     def step(self, fold=True, advect=None):
         """One implicit step (v) in place (after the advection pre-step if ``advect``, default
-        the solver's setting), then e_h += e_c; returns the step statistics."""
+        the solver's setting), then e_h += e_c; returns the step statistics.  On error the
+        state is unchanged (the pre-step writes scratch buffers that are swapped in only when
+        the implicit step succeeds)."""
         L = _rt.lib()
-        if (self.advection if advect is None else advect) and self.has_v:
-            self.advect()
         stats = _rt.StepStats()
         inp = self.inputs()
-        st = self.state()
+        adv = (self.advection if advect is None else advect) and self.has_v
+        if adv:
+            E_s, n_s, rho_s = self._advect_to_scratch(inp)
+            inp.rho_b = _rt.ptr(rho_s)
+            st = self.state(E_s, n_s)
+        else:
+            st = self.state()
         code = L.rt_implicit_step(self.handle, ctypes.byref(inp), ctypes.byref(st), ctypes.byref(stats))
         if code != _rt.RT_OK:
             err = _rt.RTError(code, "rt_implicit_step")
             err.stats = stats.as_dict()
             raise err
+        if adv:
+            (self.E, self.nHI, self.rho), self._adv = self._adv, (self.E, self.nHI, self.rho)
         if fold and not self.w["isothermal"]:
             _rt.check(L.rt_fold_energy(self.handle, _rt.ptr(self.e_h), _rt.ptr(self.ec)), "rt_fold_energy")
         self.t += self.dt
         self.stats.append(stats.as_dict())
         return self.stats[-1]
 
-    def advect(self):
-        """Advection pre-step (step (iv) for rho_b, n_HI and E, donor cell) over this step's
-        dt, in place; returns the largest Courant number."""
+    # failures after which a smaller step is worth trying
+    RETRY_CODES = (_rt.RT_ENOCONV, _rt.RT_ELINESEARCH, _rt.RT_ENONFINITE, _rt.RT_ELINEAR)
+
+    def advance(self, t_end, tau_tol=1e-3, dt_max=None, growth=2.0, max_halvings=30, newton_target=8):
+        """Steps from the current time to t_end with the time step chosen from the solution
+        change: after a step with scaled change eps (``change_norm`` of the step statistics),
+        the next step is dt min(growth, tau_tol / eps), capped by dt_max and t_end.  A step the
+        solver fails on is retried with half the step (the state is unchanged on failure); the
+        step after a retry does not grow, nor does one after a step that needed more than
+        ``newton_target`` Newton iterations (beyond 1.5 x that target it shrinks by 0.7).
+        Starts from the solver's current dt and leaves the next proposed step there; returns
+        [(t, dt, stats)] of the accepted steps (stats gain ``rejected``: retries before it)."""
+        out = []
+        dt = self.dt
+        while self.t < t_end * (1.0 - 1e-12):
+            dt = min(dt, t_end - self.t)
+            if dt_max is not None:
+                dt = min(dt, dt_max)
+            rejected = 0
+            while True:
+                self.dt = dt
+                try:
+                    st = self.step()
+                    break
+                except _rt.RTError as e:
+                    if e.code not in self.RETRY_CODES or rejected >= max_halvings:
+                        raise
+                    rejected += 1
+                    dt *= 0.5
+            st["rejected"] = rejected
+            out.append((self.t, dt, st))
+            eps = st["change_norm"]
+            factor = growth if eps <= tau_tol / growth else tau_tol / eps
+            if rejected or st["newton_iters"] > newton_target:
+                factor = min(factor, 1.0)
+            if st["newton_iters"] > 1.5 * newton_target:
+                factor = min(factor, 0.7)
+            dt *= factor
+            self.dt = dt            # the proposal carries over to the next call
+        return out
+
+    def _advect_to_scratch(self, inp):
         if self._adv is None:
             self._adv = tuple(torch.empty_like(self.E) for _ in range(3))
-        inp = self.inputs()
         c = ctypes.c_double()
         src, dst = self.state(), self.state(self._adv[0], self._adv[1])
         _rt.check(_rt.lib().rt_advect(self.handle, ctypes.byref(inp), ctypes.byref(src), ctypes.byref(dst),
                                       _rt.ptr(self.rho), _rt.ptr(self._adv[2]), ctypes.byref(c)), "rt_advect")
+        self.courant = c.value
+        return self._adv
+
+    def advect(self):
+        """Advection pre-step (step (iv) for rho_b, n_HI and E, donor cell) over this step's
+        dt, in place; returns the largest Courant number."""
+        self._advect_to_scratch(self.inputs())
         (self.E, self.nHI, self.rho), self._adv = self._adv, (self.E, self.nHI, self.rho)
-        return c.value
+        return self.courant
 
     # ---------------------------------------------------------- kernel access
     def to_device(self, a, scale):

@@ -28,6 +28,12 @@ conditions, which are not available):
   local maxima) with Ndot proportional to density (total 1e52 photons/s),
   3^3 ionised blocks (x_HI = 1e-4, T = 1e4 K) around sources, elsewhere
   x_HI = 0.9999 and T = 100 K.
+* ``shapiro_giroux``     -- the four cosmological I-front problems of the verification
+  section (Table 1: q0 in {0.5, 0.05}, z0 in {4, 10}, box L0 proper at z0, H0, Omega_b):
+  uniform gas at Omega_b rho_crit (1+z0)^3 (the quoted rho_b0 for z0 = 4), fully neutral,
+  T = 1e4 K (isothermal), E = 1e-35 erg/cm^3, one monochromatic 13.6 eV corner source of
+  5e48 photons/s (octant, zero-flux walls), case-B alpha = 2.59e-13, run from z0 to z = 0
+  in steps evenly spaced in log t.
 * ``random_state``       -- random but physical states on small grids, for
   element-wise parity of single kernels.
 """
@@ -90,6 +96,37 @@ def stromgren_cosmo(n=128, z0=10.0, z_end=4.0, nsteps=500, box_kpc_comoving=400.
         ndot_total=ndot, octant=True,
         cosmology=dict(LCDM), z0=z0, z_end=z_end, nsteps=nsteps, nH=nH,
         isothermal=True, T_iso=1e4, recomb="const", spectrum=spectrum, T_B=1e5, theta=theta,
+    )
+    return w
+
+
+# Table 1 of the verification section: q0, z0, L0 [kpc, proper at z0], H0 [100 km/s/Mpc],
+# Omega_m, Omega_Lambda, Omega_b
+SG_TABLE1 = ((0.5, 4.0, 80.0, 0.5, 1.0, 0.0, 0.2),
+             (0.05, 4.0, 60.0, 1.0, 0.1, 0.0, 0.1),
+             (0.5, 10.0, 36.0, 0.5, 1.0, 0.0, 0.2),
+             (0.05, 10.0, 27.0, 1.0, 0.1, 0.0, 0.1))
+
+
+def shapiro_giroux(row, n=32, nsteps=200, ndot=5e48, theta=1.0):
+    """Row ``row`` of Table 1 (see the module docstring); comoving box L0 (1 + z0)."""
+    q0, z0, L0, h, Om, OL, Ob = SG_TABLE1[row]
+    w = _base(n, L0 * KPC * (1.0 + z0), (False, False, False))
+    shape = (w["nz"], w["ny"], w["nx"])
+    nH = Ob * RHO_CRIT_H2 * h**2 / M_H            # comoving (proper at z0: times (1 + z0)^3)
+    w.update(
+        rho_b=np.full(shape, nH * M_H),
+        T0=np.full(shape, 1e4),
+        v=tuple(np.zeros(shape) for _ in range(3)),
+        clump=np.ones(shape, np.float32),
+        E=np.full(shape, E_FLOOR),
+        nHI=np.full(shape, nH),
+        src_index=np.array([0], np.int64),
+        src_ndot=np.array([ndot / 8.0]),
+        ndot_total=ndot, octant=True,
+        cosmology=dict(q0=q0, h=h), z0=z0, z_end=0.0, nsteps=nsteps, time_steps="log", nH=nH,
+        sg=dict(q0=q0, z0=z0, L0_kpc=L0, h=h, Omega_b=Ob),
+        isothermal=True, T_iso=1e4, recomb="const", spectrum="mono", T_B=1e5, theta=theta,
     )
     return w
 
