@@ -25,6 +25,10 @@ What it computes, with the paper passage each module follows:
   complex-step Jacobian and sparse direct solves; the Schur complement of the
   linearised system written out with sparse algebra (Sec. "Algorithm"); the
   RMS norm of Eq. rmsnorm.
+* ``helium``     -- the same step for hydrogen + helium gas (Eq. electron_density's helium
+  case; species n_HI, n_HeI, n_HeII with the rest by conservation).
+* ``advection``  -- the donor-cell advection pre-step of step (iv) and its transpose.
+* ``adjoint``    -- the dense discrete adjoint of a multi-step run.
 * ``cosmology``  -- a(t) for the verification cosmologies, the Shapiro-Giroux
   I-front closed form (Eqs. SG-stromgren_radius, SG-solution, SG-tau, SG-F)
   and the expanding-universe I-front ODE.

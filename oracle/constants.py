@@ -19,6 +19,16 @@ HNU0 = 13.6 * EV                 # hydrogen ionisation threshold (paper: 13.6 eV
 SIGMA0 = 6.3e-18                 # cm^2, H photo-ionisation cross section at threshold
 ALPHA_B_PAPER = 2.59e-13         # cm^3 / s, case-B coefficient quoted by the paper
 
+# helium (hydrogen + helium chemistry): thresholds and threshold cross sections; HeI with the
+# two-term power law a_T [beta (nu/nu_T)^-s + (1 - beta)(nu/nu_T)^(-s-1)] of Osterbrock (1989),
+# HeII hydrogenic (Z = 2: sigma_0 / 4 at four times the hydrogen edge, nu^-3 like hydrogen)
+HNU_HEI = 24.59 * EV
+HNU_HEII = 54.42 * EV
+SIGMA_HEI = 7.83e-18             # cm^2
+BETA_HEI, S_HEI = 1.66, 2.05
+SIGMA_HEII = 1.58e-18            # cm^2
+M_HE_OVER_M_H = 4.0              # helium atom mass in hydrogen masses (n_He = Y rho / (4 m_H))
+
 KPC = 3.0856775814913673e21      # cm
 MPC = 1e3 * KPC
 YEAR = 3.15576e7                 # s (Julian)

@@ -169,9 +169,15 @@ def diffusion(st, E, kappa, freeze=False):
     return out
 
 
-def opacity(st, nHI):
-    """Proper opacity kappa = sigma_E n_HI / a^3 [1/cm]."""
-    return st.sigma_E * nHI / st.a**3
+def opacity(st, nHI, nHe=None):
+    """Proper opacity kappa = sigma_E n_HI / a^3 [1/cm]; with helium (``oracle.helium``) also
+    sigma_E,HeI n_HeI + sigma_E,HeII n_HeII, from nHe = (n_HeI, n_HeII) or, if None, the
+    step's starting values."""
+    k = st.sigma_E * nHI
+    if getattr(st, "helium", False):
+        nHeI, nHeII = (st.nHeI_n, st.nHeII_n) if nHe is None else nHe
+        k = k + st.sigma_E_HeI * nHeI + st.sigma_E_HeII * nHeII
+    return k / st.a**3
 
 
 def emissivity(st):
@@ -182,9 +188,9 @@ def emissivity(st):
     return src.reshape(st.shape)
 
 
-def radiation_rhs(st, E, nHI, src, freeze=False):
+def radiation_rhs(st, E, nHI, src, freeze=False, nHe=None):
     """The bracket of Eq. radiation_residual: div(D grad E) - (adot/a) E + 4 pi eta - c kappa E."""
-    kappa = opacity(st, nHI)
+    kappa = opacity(st, nHI, nHe)
     return diffusion(st, E, kappa, freeze) - (st.adot / st.a) * E + src - K.C_LIGHT * kappa * E
 
 

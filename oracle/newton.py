@@ -71,13 +71,18 @@ def _scales(st, U):
     return np.stack([s_e, s_n, s_E]).reshape(_FIELDS, -1)
 
 
-def jacobian(st, U, bE=None, freeze=False, h=1e-30):
+def jacobian(st, U, bE=None, freeze=False, h=1e-30, residual=None, scales=None):
     """Sparse 3N x 3N Jacobian of ``model.residual`` by coloured complex steps.
 
     Unknowns and equations are ordered [e_c (N), n_HI (N), E (N)], cells flat [z,y,x].
+    ``residual`` / ``scales`` substitute another cell-local model with the same stencil
+    (hydrogen + helium: ``oracle.helium``); the field count is U's first dimension.
     """
     if bE is None:
         bE = M.explicit_part(st)
+    residual = M.residual if residual is None else residual
+    scales = _scales if scales is None else scales
+    nf = np.shape(U)[0]
     N = st.N
     for n, per in zip((st.nx, st.ny, st.nz), st.periodic):
         if per and n < 3:
@@ -89,27 +94,27 @@ def jacobian(st, U, bE=None, freeze=False, h=1e-30):
     z, y, x = np.indices(st.shape)
     colour = ((x % mx) + mx * ((y % my) + my * (z % mz))).ravel()
     ncol = mx * my * mz
-    scale = _scales(st, U)
+    scale = scales(st, U)
     nbrs = [_neighbour(st, o) for o in _offsets()]
     rows, cols, vals = [], [], []
-    for fi in range(_FIELDS):
+    for fi in range(nf):
         for c in range(ncol):
-            pert = np.zeros((_FIELDS, N), complex)
+            pert = np.zeros((nf, N), complex)
             sel = colour == c
             pert[fi, sel] = 1j * h * scale[fi, sel]
-            Uc = U.astype(complex) + pert.reshape((_FIELDS,) + st.shape)
-            fc = np.imag(M.residual(st, Uc, bE, freeze)).reshape(_FIELDS, N) / h
+            Uc = U.astype(complex) + pert.reshape((nf,) + st.shape)
+            fc = np.imag(residual(st, Uc, bE, freeze)).reshape(nf, N) / h
             for nb, valid in nbrs:
                 r = np.nonzero(valid & (colour[nb] == c))[0]
                 cc = nb[r]
-                for fo in range(_FIELDS):
+                for fo in range(nf):
                     v = fc[fo, r] / scale[fi, cc]
                     nz = v != 0.0
                     rows.append(fo * N + r[nz])
                     cols.append(fi * N + cc[nz])
                     vals.append(v[nz])
     J = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                      shape=(_FIELDS * N, _FIELDS * N))
+                      shape=(nf * N, nf * N))
     return J
 
 

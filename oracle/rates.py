@@ -52,3 +52,56 @@ def cooling_rate(T, n_e, n_HI, n_HII, a):
     T_cmb = K.T_CMB0 / a
     comp = 4.0 * K.K_BOLTZ * K.SIGMA_T * K.A_RAD * T_cmb**4 / (K.M_E * K.C_LIGHT) * (T - T_cmb) * n_e
     return rec + ce + ff + comp
+
+
+# ------------------------------------------------------------------------ helium
+# Readings for hydrogen + helium gas (Sec. "Physical Model", Eq. electron_density; the paper
+# cites Cen (1992), Hui & Gnedin (1997) and Abel et al. (1997) for the rates):
+#   case-B radiative recombination HeII -> HeI and HeIII -> HeII (Hui & Gnedin 1997), the
+#   dielectronic recombination of HeII (Aldrovandi & Pequignot form used by Cen 1992), their
+#   recombination cooling, collisional excitation of HeII (Cen 1992), bremsstrahlung with
+#   Z^2 = 4 for HeIII.  Collisional ionisation and HeI collisional excitation are left out,
+#   like hydrogen's collisional ionisation.  Parity unpinned (implementation against
+#   implementation only).
+T_HEI = 285335.0    # K, HeI ionisation temperature of the Hui & Gnedin fits
+T_HEII = 631515.0   # K, HeII
+
+
+def alpha_HeII_B(T):
+    """HeII -> HeI case-B radiative recombination [cm^3/s]."""
+    T = _cmax(T, T_FLOOR)
+    return 1.26e-14 * (2.0 * T_HEI / T) ** 0.750
+
+
+def alpha_HeIII_B(T):
+    """HeIII -> HeII case-B recombination [cm^3/s] (hydrogenic, Z = 2)."""
+    T = _cmax(T, T_FLOOR)
+    lam = 2.0 * T_HEII / T
+    return 5.506e-14 * lam**1.5 / (1.0 + (lam / 2.740) ** 0.407) ** 2.242
+
+
+def alpha_di(T):
+    """HeII dielectronic recombination [cm^3/s]."""
+    T = _cmax(T, T_FLOOR)
+    return 1.90e-3 * T**-1.5 * np.exp(-470000.0 / T) * (1.0 + 0.3 * np.exp(-94000.0 / T))
+
+
+def cooling_rate_he(T, n_e, n_HI, n_HII, n_HeII, n_HeIII, a):
+    """Total cooling of hydrogen + helium gas per unit proper volume [erg cm^-3 s^-1]:
+    the hydrogen terms of ``cooling_rate`` (with bremsstrahlung of all ions) plus HeII and
+    HeIII recombination cooling, dielectronic recombination cooling and collisional
+    excitation of HeII."""
+    T = _cmax(T, T_FLOOR)
+    lam = 2.0 * T_HI / T
+    rec = 3.435e-30 * T * lam**1.970 / (1.0 + (lam / 2.250) ** 0.376) ** 3.720 * n_e * n_HII
+    ce = 7.5e-19 * np.exp(-118348.0 / T) / (1.0 + np.sqrt(T / 1e5)) * n_e * n_HI
+    gff = 1.1 + 0.34 * np.exp(-((5.5 - np.log10(T)) ** 2) / 3.0)
+    ff = 1.42e-27 * gff * np.sqrt(T) * n_e * (n_HII + n_HeII + 4.0 * n_HeIII)
+    T_cmb = K.T_CMB0 / a
+    comp = 4.0 * K.K_BOLTZ * K.SIGMA_T * K.A_RAD * T_cmb**4 / (K.M_E * K.C_LIGHT) * (T - T_cmb) * n_e
+    rec_he2 = K.K_BOLTZ * T * alpha_HeII_B(T) * n_e * n_HeII
+    lam3 = 2.0 * T_HEII / T
+    rec_he3 = 8.0 * 3.435e-30 * T * lam3**1.970 / (1.0 + (lam3 / 2.250) ** 0.376) ** 3.720 * n_e * n_HeIII
+    di = 6.526e-11 * alpha_di(T) * n_e * n_HeII
+    ce_he2 = 5.54e-17 * T**-0.397 * np.exp(-473638.0 / T) / (1.0 + np.sqrt(T / 1e5)) * n_e * n_HeII
+    return rec + ce + ff + comp + rec_he2 + rec_he3 + di + ce_he2

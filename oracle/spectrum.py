@@ -20,7 +20,8 @@ deposited per unit absorbed energy follows as (sigma_E - h nu_0 sigma_G).
 Computed here with adaptive quadrature (scipy.integrate.quad) in x = h nu / k T_B.
 Pinned in tests against closed forms: the Bose-Einstein series for the moments
 of x^n/(e^x - 1), -ln(1 - e^-x0) for the nu^-3-weighted moment, and the exact
-monochromatic limits.
+monochromatic limits.  ``helium_grey_constants`` does the same for the HeI and HeII
+cross sections above their own thresholds (pinned against the incomplete-gamma series).
 """
 import math
 
@@ -57,3 +58,31 @@ def grey_constants(spectrum="blackbody", T_B=1e5):
     sigma_G = K.SIGMA0 * x0**3 * sm1 / (kT * e3)
     eps_src = kT * e3 / e2
     return dict(sigma_E=sigma_E, sigma_G=sigma_G, eps_src=eps_src)
+
+
+def _bb_or_mono_norm(spectrum, T_B):
+    kT = K.K_BOLTZ * T_B
+    return kT, K.HNU0 / kT, _bb_moment(lambda x: x**3, K.HNU0 / kT)
+
+
+def helium_grey_constants(spectrum="blackbody", T_B=1e5):
+    """Grey constants of the helium species over the same chi_E (normalised by the energy
+    above the hydrogen edge, since E integrates from nu_0): dict(sigma_E_HeI, sigma_G_HeI,
+    sigma_E_HeII, sigma_G_HeII).  The cross sections vanish below each threshold; a
+    monochromatic 13.6 eV spectrum leaves helium un-ionised (all zero)."""
+    if spectrum == "mono":
+        return dict(sigma_E_HeI=0.0, sigma_G_HeI=0.0, sigma_E_HeII=0.0, sigma_G_HeII=0.0)
+    if spectrum != "blackbody":
+        raise ValueError(spectrum)
+    kT, x0, e3 = _bb_or_mono_norm(spectrum, T_B)
+    out = {}
+    # HeI: a_T [beta (x1/x)^s + (1 - beta)(x1/x)^(s+1)] x^3 / (e^x - 1), x >= x1
+    x1, s, b = K.HNU_HEI / kT, K.S_HEI, K.BETA_HEI
+    shape1 = lambda x, p: K.SIGMA_HEI * (b * (x1 / x) ** s + (1 - b) * (x1 / x) ** (s + 1)) * x**p
+    out["sigma_E_HeI"] = _bb_moment(lambda x: shape1(x, 3), x1) / e3
+    out["sigma_G_HeI"] = _bb_moment(lambda x: shape1(x, 2), x1) / (kT * e3)
+    # HeII: sigma_2 (x2/x)^3 x^3 / (e^x - 1), x >= x2
+    x2 = K.HNU_HEII / kT
+    out["sigma_E_HeII"] = K.SIGMA_HEII * x2**3 * _bb_moment(lambda x: 1.0, x2) / e3
+    out["sigma_G_HeII"] = K.SIGMA_HEII * x2**3 * _bb_moment(lambda x: 1.0 / x, x2) / (kT * e3)
+    return out

@@ -36,6 +36,8 @@ conditions, which are not available):
   in steps evenly spaced in log t.
 * ``random_state``       -- random but physical states on small grids, for
   element-wise parity of single kernels.
+* ``with_helium``        -- the hydrogen + helium version of any of them (helium mass
+  fraction Y = 0.24, helium singly ionised where hydrogen is ionised).
 """
 import numpy as np
 
@@ -128,6 +130,18 @@ def shapiro_giroux(row, n=32, nsteps=200, ndot=5e48, theta=1.0):
         sg=dict(q0=q0, z0=z0, L0_kpc=L0, h=h, Omega_b=Ob),
         isothermal=True, T_iso=1e4, recomb="const", spectrum="mono", T_B=1e5, theta=theta,
     )
+    return w
+
+
+def with_helium(w, Y=0.24):
+    """Hydrogen + helium version of workload w: helium mass fraction Y (n_H = (1 - Y) rho / m_H,
+    n_He = Y rho / (4 m_H)), the hydrogen neutral fraction kept, and helium singly ionised
+    where hydrogen is ionised (n_HeI = x_HI n_He, n_HeII = (1 - x_HI) n_He, no HeIII)."""
+    w = dict(w)
+    rho = np.asarray(w["rho_b"], float)
+    xHI = np.asarray(w["nHI"], float) * M_H / rho
+    nHe = Y * rho / (4.0 * M_H)
+    w.update(helium=True, Y=Y, nHI=xHI * (1.0 - Y) * rho / M_H, nHeI=xHI * nHe, nHeII=(1.0 - xHI) * nHe)
     return w
 
 
