@@ -71,6 +71,11 @@ typedef struct {
     double T_B;           /* blackbody temperature, K                                        */
     int recomb;           /* RT_RECOMB_CONST (alpha_B = 2.59e-13) or RT_RECOMB_HG97           */
     int cooling;          /* non-isothermal runs: 1 = include Lambda                          */
+    int helium;           /* 0: hydrogen only (n_H = rho / m_H); 1: hydrogen + helium with
+                             mass fraction Y (n_H = (1-Y) rho / m_H, n_He = Y rho / (4 m_H)),
+                             species n_HI, n_HeI, n_HeII in the state, n_e = n_HII + n_HeII +
+                             2 n_HeIII (Eq. electron_density with number densities)          */
+    double Y;             /* helium mass fraction, 0 <= Y < 1 (helium = 1)                   */
     int limiter;          /* RT_LIMITER_LAGGED (Eq. limiter at the step's start state) or
                              RT_LIMITER_CONST (D = D_const, a test mode)                      */
     double D_const;       /* proper diffusion coefficient for RT_LIMITER_CONST, cm^2/s        */
@@ -104,6 +109,8 @@ typedef struct {
     double* E;            /* radiation energy density                                        */
     double* n_HI;         /* neutral hydrogen number density                                 */
     double* e_c;          /* gas energy correction of step (v) (specific)                    */
+    double* n_HeI;        /* helium grids only: neutral and singly ionised helium number     */
+    double* n_HeII;       /* densities (n_HeIII = n_He - n_HeI - n_HeII); unused otherwise   */
 } rt_state;
 
 #define RT_STATS_HIST 64
@@ -176,6 +183,12 @@ typedef struct {
 } rt_kernel_profile;
 int rt_set_profiling(rt_grid* g, int on);
 int rt_get_profile(rt_grid* g, rt_kernel_profile* out, int max_entries, int* n_entries);
+
+/* Helium grids: rt_residual with the two helium species' residuals f_HeI, f_HeII as well
+ * (all outputs optional, NULL skips).  U_n and U must carry n_HeI and n_HeII.  Errors as
+ * rt_residual, and RT_EINVAL on a hydrogen-only grid. */
+int rt_residual_helium(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U,
+                       double* f_e, double* f_n, double* f_HeI, double* f_HeII, double* f_E);
 
 /* Diagnostic: evaluates the library's table-driven FP64 exp (fn 0) or log (fn 1) used by the
  * rate fits, or the CUDA math library's exp (fn 2) / log (fn 3), on n device values x into y,

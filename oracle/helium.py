@@ -307,3 +307,47 @@ def rms(w, f):
     """Eq. rmsnorm over the N (N_s + 2) = 5 N unknowns."""
     v = (w * np.real(f)).ravel()
     return float(np.sqrt(np.dot(v, v) / v.size))
+
+
+def energy_from_temperature(T, rho_b, nHI, nHeI, nHeII, Y, v):
+    """Specific total energy for temperature T of hydrogen + helium gas (Eqs. eos, temperature
+    with n_tot = n_H + n_He + n_e)."""
+    nH = (1.0 - Y) * rho_b / K.M_H
+    nHe = Y * rho_b / (K.M_HE_OVER_M_H * K.M_H)
+    n_tot = nH + nHe + (nH - nHI) + nHeII + 2.0 * (nHe - nHeI - nHeII)
+    return K.K_BOLTZ * T * n_tot / ((K.GAMMA - 1.0) * rho_b) + 0.5 * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2)
+
+
+class Run:
+    """Multi-step oracle run of a hydrogen + helium workload (``workloads.with_helium``)."""
+
+    def __init__(self, w, theta=None):
+        from . import driver
+        from . import spectrum as S
+        self._h = driver.Run(w, theta)              # hydrogen bookkeeping: time, grey constants
+        self.w = w
+        self.Y = w["Y"]
+        self.helium_grey = S.helium_grey_constants(w["spectrum"], w.get("T_B", 1e5))
+        self.nHeI = np.array(w["nHeI"], float)
+        self.nHeII = np.array(w["nHeII"], float)
+        self._h.e_h = energy_from_temperature(w["T0"], w["rho_b"], self._h.nHI, self.nHeI, self.nHeII, self.Y, w["v"])
+
+    def make_step(self):
+        from dataclasses import fields
+        base = self._h.make_step()
+        kw = {f.name: getattr(base, f.name) for f in fields(base)}
+        return HeStep(**kw, Y=self.Y, nHeI_n=self.nHeI, nHeII_n=self.nHeII, **self.helium_grey)
+
+    def advance(self, tol=1e-11):
+        st = self.make_step()
+        U, info = solve_step(st, tol=tol)
+        e_c, nHI, nHeI, nHeII, E = U
+        self._h.E, self._h.nHI = E, nHI
+        self.nHeI, self.nHeII = nHeI, nHeII
+        self._h.e_h = self._h.e_h + e_c
+        self._h.t += self._h.dt
+        return U, info
+
+    @property
+    def t(self):
+        return self._h.t

@@ -30,7 +30,7 @@ class GridDesc(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("isothermal", ctypes.c_int), ("T_iso", ctypes.c_double),
         ("spectrum", ctypes.c_int), ("T_B", ctypes.c_double),
-        ("recomb", ctypes.c_int), ("cooling", ctypes.c_int),
+        ("recomb", ctypes.c_int), ("cooling", ctypes.c_int), ("helium", ctypes.c_int), ("Y", ctypes.c_double),
         ("limiter", ctypes.c_int), ("D_const", ctypes.c_double),
         ("E_min", ctypes.c_double),
         ("newton_tol", ctypes.c_double), ("max_newton", ctypes.c_int),
@@ -52,7 +52,8 @@ class StepInputs(ctypes.Structure):
 
 
 class State(ctypes.Structure):
-    _fields_ = [("E", ctypes.c_void_p), ("n_HI", ctypes.c_void_p), ("e_c", ctypes.c_void_p)]
+    _fields_ = [("E", ctypes.c_void_p), ("n_HI", ctypes.c_void_p), ("e_c", ctypes.c_void_p),
+                ("n_HeI", ctypes.c_void_p), ("n_HeII", ctypes.c_void_p)]
 
 
 class StepStats(ctypes.Structure):
@@ -85,7 +86,7 @@ _lib = None
 EXPORTS = ["rt_init_grid", "rt_implicit_step", "rt_residual", "rt_schur_system", "rt_schur_solve",
            "rt_adjoint_step", "rt_fold_energy", "rt_destroy_grid", "rt_error_string",
            "rt_last_error_detail", "rt_grey_constants", "rt_set_profiling", "rt_get_profile",
-           "rt_residual_static", "rt_eval_elementary", "rt_advect", "rt_advect_adjoint"]
+           "rt_residual_static", "rt_eval_elementary", "rt_advect", "rt_advect_adjoint", "rt_residual_helium"]
 
 
 def lib():
@@ -100,6 +101,7 @@ def lib():
     L.rt_init_grid.argtypes = [P(GridDesc), P(ctypes.c_void_p)]
     L.rt_implicit_step.argtypes = [ctypes.c_void_p, P(StepInputs), P(State), P(StepStats)]
     L.rt_residual.argtypes = [ctypes.c_void_p, P(StepInputs), P(State), P(State)] + [ctypes.c_void_p] * 3
+    L.rt_residual_helium.argtypes = [ctypes.c_void_p, P(StepInputs), P(State), P(State)] + [ctypes.c_void_p] * 5
     L.rt_schur_system.argtypes = [ctypes.c_void_p, P(StepInputs), P(State), P(State)] + [ctypes.c_void_p] * 5
     L.rt_schur_solve.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
                                  P(ctypes.c_int)]

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(HERE, "lib", "obj")
 LIB = os.path.join(LIBDIR, "librtfld.so")
-SOURCES = ["kernels_step.cu", "kernels_solve.cu", "kernels_adjoint.cu", "kernels_advect.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["kernels_step.cu", "kernels_solve.cu", "kernels_adjoint.cu", "kernels_advect.cu", "kernels_helium.cu", "capi.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -33,6 +33,9 @@ constexpr double kGamma = 5.0 / 3.0;
 constexpr double kHnu0 = 13.6 * kEV;
 constexpr double kSigma0 = 6.3e-18;
 constexpr double kAlphaB = 2.59e-13;
+// helium: thresholds, threshold cross sections (HeI: Osterbrock's two-term power law)
+constexpr double kHnuHeI = 24.59 * kEV, kHnuHeII = 54.42 * kEV;
+constexpr double kSigmaHeI = 7.83e-18, kBetaHeI = 1.66, kSHeI = 2.05, kSigmaHeII = 1.58e-18;
 
 thread_local char g_detail[512] = "";
 
@@ -46,7 +49,8 @@ void set_detail(const char* fmt, ...) {
 // ---------------------------------------------------------------- spectral averages
 // int_{x0}^{inf} f(x) / (e^x - 1) dx by composite 16-point Gauss-Legendre on panels of
 // width 0.25 out to x0 + 80 (the integrand falls as e^-x).
-double bose_integral(double (*f)(double), double x0) {
+template <class F>
+double bose_integral(F f, double x0) {
     static const double gx[8] = {0.0950125098376374, 0.2816035507792589, 0.4580167776572274, 0.6178762444026438,
                                  0.7554044083550030, 0.8656312023878318, 0.9445750230732326, 0.9894009349916499};
     static const double gw[8] = {0.1894506104550685, 0.1826034150449236, 0.1691565193950025, 0.1495959888165767,
@@ -92,6 +96,27 @@ Grey grey_constants(int spectrum, double T_B) {
     return g;
 }
 
+// grey constants of HeI and HeII over the same spectrum (normalised by the energy above the
+// hydrogen edge): sigma_E,i and sigma_G,i; zero for the 13.6 eV line
+struct GreyHe {
+    double sE1, sG1, sE2, sG2;
+};
+
+GreyHe helium_grey_constants(int spectrum, double T_B) {
+    GreyHe h = {0.0, 0.0, 0.0, 0.0};
+    if (spectrum == RT_SPECTRUM_MONO) return h;
+    const double kT = kKB * T_B, x0 = kHnu0 / kT, x1 = kHnuHeI / kT, x2 = kHnuHeII / kT;
+    const double e3 = bose_integral(w_x3, x0);
+    auto s1 = [x1](double x) {
+        return kSigmaHeI * (kBetaHeI * std::pow(x1 / x, kSHeI) + (1.0 - kBetaHeI) * std::pow(x1 / x, kSHeI + 1.0));
+    };
+    h.sE1 = bose_integral([&](double x) { return s1(x) * x * x * x; }, x1) / e3;
+    h.sG1 = bose_integral([&](double x) { return s1(x) * x * x; }, x1) / (kT * e3);
+    h.sE2 = kSigmaHeII * x2 * x2 * x2 * bose_integral(w_1, x2) / e3;
+    h.sG2 = kSigmaHeII * x2 * x2 * x2 * bose_integral(w_xm1, x2) / (kT * e3);
+    return h;
+}
+
 // ------------------------------------------------------------------ device buffers
 
 template <class T>
@@ -131,6 +156,7 @@ struct rt_grid {
     double *Ec, *nc, *ecc, *Et, *nt, *ect;
     double *step, *diag, *rhs, *wE;
     double *Xec, *Xnc, *Xet, *Xnt;   // local-elimination sensitivities (current / trial)
+    double *He10, *He20, *He1c, *He2c, *He1t, *He2t;   // helium: start, current, trial (n_HeI, n_HeII)
     // CG vectors
     double *x, *r, *z, *p, *q;
     // multigrid
@@ -434,11 +460,20 @@ PhysParams step_params(const rt_grid* g, const rt_step_inputs* in) {
 
 // sources, faces, explicit part, initial iterate into (Ec, nc, ecc); sets P.E_floor
 int step_setup(rt_grid* g, const rt_step_inputs* in, PhysParams& P, const double* E_start,
-               const double* n_start) {
+               const double* n_start, const double* he1_start = nullptr, const double* he2_start = nullptr) {
     cudaStream_t s = g->stream;
     const long long n = g->n;
     RT_CUDA(cudaMemcpyAsync(g->E0, E_start, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     RT_CUDA(cudaMemcpyAsync(g->n0, n_start, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (g->desc.helium) {
+        // start copies (their opacity enters D^n and b_E) and the initial iterate's helium
+        RT_CUDA(cudaMemcpyAsync(g->He10, he1_start, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        RT_CUDA(cudaMemcpyAsync(g->He20, he2_start, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        RT_CUDA(cudaMemcpyAsync(g->He1c, he1_start, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        RT_CUDA(cudaMemcpyAsync(g->He2c, he2_start, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        P.nHeI0 = g->He10;
+        P.nHeII0 = g->He20;
+    }
     RT_CUDA(cudaMemsetAsync(g->d_err, 0, sizeof(int), s));
     const double N = (double)n;
     run(g, K_ZERO, N * 8, [&] { launch_zero(g->src, n, s); });
@@ -490,6 +525,10 @@ AssembleArgs base_args(rt_grid* g, const rt_step_inputs* in) {
 // Courant bound first, so nothing is written when it fails.
 int advect_call(rt_grid* g, const rt_step_inputs* in, const rt_state* src, rt_state* dst, const double* rho_src,
                 double* rho_dst, double* courant_max, bool transpose) {
+    if (g && g->desc.helium) {
+        set_detail("the advection pre-step covers hydrogen-only grids");
+        return RT_EINVAL;
+    }
     if (!g || !in || !src || !dst || !src->E || !src->n_HI || !dst->E || !dst->n_HI || (!rho_src != !rho_dst)) {
         set_detail("null grid, inputs or state array (rho_src and rho_dst must be both set or both NULL)");
         return RT_EINVAL;
@@ -623,7 +662,8 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out) {
             return RT_EINVAL;
         }
     if ((d.precision != RT_FP64 && d.precision != RT_MIXED) || d.mg_nu1 < 1 || d.mg_nu2 < 1 || d.max_newton < 1 ||
-        d.max_lin < 1 || !(d.newton_tol > 0) || !(d.lin_rtol > 0)) {
+        d.max_lin < 1 || !(d.newton_tol > 0) || !(d.lin_rtol > 0) || (d.helium != 0 && d.helium != 1) ||
+        (d.helium && !(d.Y >= 0.0 && d.Y < 1.0))) {
         set_detail("invalid solver parameters");
         return RT_EINVAL;
     }
@@ -683,6 +723,17 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out) {
     P.src_scale = g->grey.eps_src * d.u_t / (d.u_x * d.u_x * d.u_x * g->u_E * d.dx * d.dx * d.dx);
     P.alpha_const = kAlphaB;
     P.isothermal = d.isothermal;
+    P.helium = d.helium;
+    P.Y = d.helium ? d.Y : 0.0;
+    if (d.helium) {
+        const GreyHe h = helium_grey_constants(d.spectrum, d.T_B);
+        P.kE1 = h.sE1 * g->u_n * d.u_x;
+        P.kE2 = h.sE2 * g->u_n * d.u_x;
+        P.kG1 = kC * h.sG1 * g->u_E * d.u_t;
+        P.kG2 = kC * h.sG2 * g->u_E * d.u_t;
+        P.kH1 = kC * g->u_n * (h.sE1 - kHnuHeI * h.sG1) * d.u_t;
+        P.kH2 = kC * g->u_n * (h.sE2 - kHnuHeII * h.sG2) * d.u_t;
+    }
     P.recomb = d.recomb;
     P.cooling = d.cooling;
     P.limiter = d.limiter;
@@ -692,6 +743,10 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out) {
     double** fp64[] = {&g->E0, &g->n0, &g->src, &g->bE, &g->wx, &g->wy, &g->wz, &g->Ec, &g->nc, &g->ecc, &g->Et,
                        &g->nt, &g->ect, &g->step, &g->diag, &g->rhs, &g->wE, &g->x, &g->r, &g->z, &g->p, &g->q};
     for (double** b : fp64) *b = dalloc<double>(n, ok);
+    if (d.helium) {
+        double** he[] = {&g->He10, &g->He20, &g->He1c, &g->He2c, &g->He1t, &g->He2t};
+        for (double** b : he) *b = dalloc<double>(n, ok);
+    }
     if (!d.isothermal) {
         g->Xec = dalloc<double>(n, ok);
         g->Xnc = dalloc<double>(n, ok);
@@ -754,8 +809,8 @@ int rt_grey_constants(const rt_grid* g, double* sigma_E, double* sigma_G, double
 }
 
 int rt_implicit_step(rt_grid* g, const rt_step_inputs* in, rt_state* io, rt_step_stats* stats) {
-    if (!g || !io || !io->E || !io->n_HI || !io->e_c) {
-        set_detail("null grid or state");
+    if (!g || !io || !io->E || !io->n_HI || !io->e_c || (g->desc.helium && (!io->n_HeI || !io->n_HeII))) {
+        set_detail("null grid or state array");
         return RT_EINVAL;
     }
     int rc = validate_inputs(g, in);
@@ -763,12 +818,18 @@ int rt_implicit_step(rt_grid* g, const rt_step_inputs* in, rt_state* io, rt_step
     RT_CUDA(cudaSetDevice(g->desc.device));
     g->launches = 0;
     PhysParams P = step_params(g, in);
-    rc = step_setup(g, in, P, io->E, io->n_HI);
+    rc = step_setup(g, in, P, io->E, io->n_HI, io->n_HeI, io->n_HeII);
     if (rc) return rc;
     cudaStream_t s = g->stream;
     const long long n = g->n;
+    const bool he = g->desc.helium != 0;
+    const double nunk = (he ? 5.0 : 3.0) * (double)n;   // N (N_s + 2) unknowns of Eq. rmsnorm
     rt_step_stats st;
     std::memset(&st, 0, sizeof(st));
+    HeliumArgs H;
+    std::memset(&H, 0, sizeof(H));
+    H.nHeI0 = g->He10;
+    H.nHeII0 = g->He20;
 
     AssembleArgs A = base_args(g, in);
     double lam = 0.0;
@@ -787,22 +848,28 @@ int rt_implicit_step(rt_grid* g, const rt_step_inputs* in, rt_state* io, rt_step
         A.diag = g->diag;
         A.rhs = g->rhs;
         A.wE = g->wE;
-        A.Xe_cur = have_cur ? g->Xec : nullptr;
-        A.Xn_cur = have_cur ? g->Xnc : nullptr;
-        A.Xe_out = g->Xet;
-        A.Xn_out = g->Xnt;
+        A.Xe_cur = have_cur && !he ? g->Xec : nullptr;
+        A.Xn_cur = have_cur && !he ? g->Xnc : nullptr;
+        A.Xe_out = he ? nullptr : g->Xet;
+        A.Xn_out = he ? nullptr : g->Xnt;
+        H.HeI_guess = g->He1c;
+        H.HeII_guess = g->He2c;
+        H.HeI_out = g->He1t;
+        H.HeII_out = g->He2t;
         // algorithmic bytes per cell: E_k, n guess, E^n, n^n, rho, e_h, b_E, src, 3 faces read;
         // trial E, n, e_c, Schur diagonal, right side and norm weight written
         double per = 8.0 * (1 + 1 + 4 + 2 + 3) + 4.0 + 8.0 * 6;
         if (A.step) per += 8.0;
         if (!P.isothermal) per += 8.0 + (in->vx ? 24.0 : 0.0) + 16.0 + (have_cur ? 16.0 : 0.0);
         int nb = 0;
-        run(g, K_ASSEMBLE, (double)n * per, [&] { nb = launch_assemble(P, A, false, s); });
+        if (he) per += 8.0 * 6;
+        run(g, K_ASSEMBLE, (double)n * per,
+            [&] { nb = he ? launch_assemble_he(P, A, H, false, s) : launch_assemble(P, A, false, s); });
         st.residual_evals++;
         double v[3];
         rc = read_scalars(g, nb, 3, v);
         if (rc) return rc;
-        const double scale = 1.0 / (3.0 * (double)n);
+        const double scale = 1.0 / nunk;
         const double n_armijo = std::sqrt(v[0] * scale), n_own = std::sqrt(v[1] * scale);
         if (st.nhist < RT_STATS_HIST) {
             st.hist_norm[st.nhist] = have_cur ? n_armijo : n_own;
@@ -839,6 +906,8 @@ int rt_implicit_step(rt_grid* g, const rt_step_inputs* in, rt_state* io, rt_step
         swap_ptr(g->ecc, g->ect);
         swap_ptr(g->Xec, g->Xet);
         swap_ptr(g->Xnc, g->Xnt);
+        swap_ptr(g->He1c, g->He1t);
+        swap_ptr(g->He2c, g->He2t);
         if (!have_cur) st.norm0 = n_own;
         else st.newton_iters++;
         have_cur = true;
@@ -872,13 +941,15 @@ int rt_implicit_step(rt_grid* g, const rt_step_inputs* in, rt_state* io, rt_step
         A.E_cur = g->Ec;
         A.n_guess = g->nc;
         A.ec_guess = g->ecc;
+        H.HeI_guess = g->He1c;
+        H.HeII_guess = g->He2c;
         int nb = 0;
-        run(g, K_RESNORM, (double)n * 8.0 * (P.isothermal ? 5 : 7 + (in->vx ? 3 : 0)),
-            [&] { nb = launch_change_norm(P, A, s); });
+        run(g, K_RESNORM, (double)n * 8.0 * (P.isothermal ? 5 : 7 + (in->vx ? 3 : 0)) + (he ? 32.0 * n : 0.0),
+            [&] { nb = he ? launch_change_norm_he(P, A, H, s) : launch_change_norm(P, A, s); });
         double v = 0.0;
         rc = read_scalars(g, nb, 1, &v);
         if (rc) return rc;
-        st.change_norm = std::sqrt(v / (3.0 * (double)n));
+        st.change_norm = std::sqrt(v / nunk);
     }
     st.kernel_launches = g->launches;
     if (stats) *stats = st;
@@ -890,18 +961,28 @@ int rt_implicit_step(rt_grid* g, const rt_step_inputs* in, rt_state* io, rt_step
     RT_CUDA(cudaMemcpyAsync(io->E, g->Ec, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     RT_CUDA(cudaMemcpyAsync(io->n_HI, g->nc, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     RT_CUDA(cudaMemcpyAsync(io->e_c, g->ecc, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (he) {
+        RT_CUDA(cudaMemcpyAsync(io->n_HeI, g->He1c, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        RT_CUDA(cudaMemcpyAsync(io->n_HeII, g->He2c, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
     RT_CUDA(cudaStreamSynchronize(s));
     return check_launch("implicit step");
 }
 
-int rt_residual(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U, double* f_e,
-                double* f_n, double* f_E) {
-    if (!g || !U_n || !U || !U_n->E || !U_n->n_HI || !U->E || !U->n_HI || !U->e_c) return RT_EINVAL;
+// f(U) for the step starting from U_n, by the Newton evaluation kernel in given-iterate mode
+int residual_call(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U, double* f_e,
+                  double* f_n, double* f_HeI, double* f_HeII, double* f_E) {
+    const bool he = g && g->desc.helium;
+    if (!g || !U_n || !U || !U_n->E || !U_n->n_HI || !U->E || !U->n_HI || !U->e_c ||
+        (he && (!U_n->n_HeI || !U_n->n_HeII || !U->n_HeI || !U->n_HeII))) {
+        set_detail("null grid or state array");
+        return RT_EINVAL;
+    }
     int rc = validate_inputs(g, in);
     if (rc) return rc;
     RT_CUDA(cudaSetDevice(g->desc.device));
     PhysParams P = step_params(g, in);
-    rc = step_setup(g, in, P, U_n->E, U_n->n_HI);
+    rc = step_setup(g, in, P, U_n->E, U_n->n_HI, U_n->n_HeI, U_n->n_HeII);
     if (rc) return rc;
     AssembleArgs A = base_args(g, in);
     A.E_cur = U->E;
@@ -910,19 +991,47 @@ int rt_residual(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const
     A.fE_out = f_E;
     A.fn_out = f_n;
     A.fe_out = f_e;
-    launch_assemble(P, A, true, g->stream);
+    if (he) {
+        HeliumArgs H;
+        std::memset(&H, 0, sizeof(H));
+        H.nHeI0 = g->He10;
+        H.nHeII0 = g->He20;
+        H.HeI_given = U->n_HeI;
+        H.HeII_given = U->n_HeII;
+        H.fHeI_out = f_HeI;
+        H.fHeII_out = f_HeII;
+        launch_assemble_he(P, A, H, true, g->stream);
+    } else {
+        launch_assemble(P, A, true, g->stream);
+    }
     RT_CUDA(cudaStreamSynchronize(g->stream));
     return check_launch("residual");
 }
 
+int rt_residual(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U, double* f_e,
+                double* f_n, double* f_E) {
+    return residual_call(g, in, U_n, U, f_e, f_n, nullptr, nullptr, f_E);
+}
+
+int rt_residual_helium(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U,
+                       double* f_e, double* f_n, double* f_HeI, double* f_HeII, double* f_E) {
+    if (g && !g->desc.helium) {
+        set_detail("rt_residual_helium needs a grid with helium");
+        return RT_EINVAL;
+    }
+    return residual_call(g, in, U_n, U, f_e, f_n, f_HeI, f_HeII, f_E);
+}
+
 int rt_schur_system(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U, double* diag,
                     double* wx, double* wy, double* wz, double* rhs) {
-    if (!g || !U_n || !U || !U_n->E || !U_n->n_HI || !U->E || !U->n_HI || !U->e_c) return RT_EINVAL;
+    if (!g || !U_n || !U || !U_n->E || !U_n->n_HI || !U->E || !U->n_HI || !U->e_c ||
+        (g->desc.helium && (!U_n->n_HeI || !U_n->n_HeII || !U->n_HeI || !U->n_HeII)))
+        return RT_EINVAL;
     int rc = validate_inputs(g, in);
     if (rc) return rc;
     RT_CUDA(cudaSetDevice(g->desc.device));
     PhysParams P = step_params(g, in);
-    rc = step_setup(g, in, P, U_n->E, U_n->n_HI);
+    rc = step_setup(g, in, P, U_n->E, U_n->n_HI, U_n->n_HeI, U_n->n_HeII);
     if (rc) return rc;
     AssembleArgs A = base_args(g, in);
     A.E_cur = U->E;
@@ -931,7 +1040,17 @@ int rt_schur_system(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, c
     A.diag = g->diag;
     A.rhs = g->rhs;
     A.wE = g->wE;
-    launch_assemble(P, A, true, g->stream);
+    if (g->desc.helium) {
+        HeliumArgs H;
+        std::memset(&H, 0, sizeof(H));
+        H.nHeI0 = g->He10;
+        H.nHeII0 = g->He20;
+        H.HeI_given = U->n_HeI;
+        H.HeII_given = U->n_HeII;
+        launch_assemble_he(P, A, H, true, g->stream);
+    } else {
+        launch_assemble(P, A, true, g->stream);
+    }
     const size_t bytes = (size_t)g->n * sizeof(double);
     cudaStream_t s = g->stream;
     if (diag) RT_CUDA(cudaMemcpyAsync(diag, g->diag, bytes, cudaMemcpyDeviceToDevice, s));
@@ -1030,6 +1149,10 @@ int rt_advect_adjoint(rt_grid* g, const rt_step_inputs* in, const rt_state* lam_
 
 int rt_adjoint_step(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U_np1,
                     const rt_state* lam_np1, rt_state* lam_n, double* g_ndot, float* g_clump) {
+    if (g && g->desc.helium) {
+        set_detail("the discrete adjoint covers hydrogen-only grids");
+        return RT_EINVAL;
+    }
     if (!g || !U_n || !U_np1 || !lam_np1 || !lam_n || !U_n->E || !U_n->n_HI || !U_np1->E || !U_np1->n_HI ||
         !U_np1->e_c || !lam_np1->E || !lam_np1->n_HI || !lam_np1->e_c || !lam_n->E || !lam_n->n_HI || !lam_n->e_c) {
         set_detail("null state or adjoint array");

@@ -74,6 +74,24 @@ int launch_assemble(const PhysParams& P, const AssembleArgs& A, bool given_u, cu
 // sum of squared scaled changes (E_cur, n_guess, ec_guess) against (E0, n0): one slot per block
 int launch_change_norm(const PhysParams& P, const AssembleArgs& A, cudaStream_t s);
 
+// ---- hydrogen + helium: the helium species next to AssembleArgs' hydrogen ones
+struct HeliumArgs {
+    const double* nHeI0;       // start of step
+    const double* nHeII0;
+    const double* HeI_guess;   // local-solve starting values (current iterate)
+    const double* HeII_guess;
+    const double* HeI_given;   // given-iterate mode
+    const double* HeII_given;
+    double* HeI_out;           // trial values
+    double* HeII_out;
+    double* fHeI_out;          // optional residual outputs
+    double* fHeII_out;
+};
+int launch_assemble_he(const PhysParams& P, const AssembleArgs& A, const HeliumArgs& H, bool given_u,
+                       cudaStream_t s);
+// change norm with the helium species (HeI_guess / HeII_guess hold the new state)
+int launch_change_norm_he(const PhysParams& P, const AssembleArgs& A, const HeliumArgs& H, cudaStream_t s);
+
 // ---- advection pre-step (donor cell) and its transpose
 struct AdvectArgs {
     int nx, ny, nz;

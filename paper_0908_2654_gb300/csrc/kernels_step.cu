@@ -9,41 +9,12 @@
 //                derivatives), radiation residual f_E (7-point), Schur diagonal and right side
 //                of the reduced Newton system (Sec. "Algorithm"), and the block partial sums of
 //                the component-scaled RMS norm (Eq. rmsnorm).
+#include "cellgrid.cuh"
 #include "kernels.cuh"
 
 namespace {
 
-constexpr int kBlock = 256;
-
-__device__ __forceinline__ void cell_coords(long long i, int nx, int ny, int& x, int& y, int& z) {
-    long long q = i / nx;
-    x = (int)(i - q * nx);
-    z = (int)(q / ny);
-    y = (int)(q - (long long)z * ny);
-}
-
-// neighbour index along an axis; at a wall the index is clamped (its face coupling is 0)
-__device__ __forceinline__ int up(int c, int n, int per) { return c + 1 < n ? c + 1 : (per ? 0 : c); }
-__device__ __forceinline__ int dn(int c, int n, int per) { return c > 0 ? c - 1 : (per ? n - 1 : c); }
-
-template <int NS>
-__device__ void block_sums(double (&v)[NS], double* partials) {
-    __shared__ double sh[NS][kBlock / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-        double s = v[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) sh[k][warp] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x < NS) {
-        double s = 0.0;
-        for (int w = 0; w < kBlock / 32; ++w) s += sh[threadIdx.x][w];
-        partials[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
-    }
-}
+using namespace cellgrid;
 
 __global__ void k_zero(double* p, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -70,7 +41,7 @@ __global__ void k_faces(PhysParams P, const double* __restrict__ E0, const doubl
         int x, y, z;
         cell_coords(i, P.nx, P.ny, x, y, z);
         const double Ei = E0[i];
-        const double ki = P.kE * n0[i] / P.a3;
+        const double ki = kappa_start(P, n0, i);
         const long long sy = P.nx, sz = (long long)P.nx * P.ny;
         const long long base = i - x - (long long)y * sy - (long long)z * sz;
         long long j[3] = {base + up(x, P.nx, P.per[0]) + y * sy + z * sz,
@@ -83,7 +54,7 @@ __global__ void k_faces(PhysParams P, const double* __restrict__ E0, const doubl
             if (wall[d]) {
                 w[d] = 0.0;
             } else {
-                const double D = limiter_face(P, Ei, E0[j[d]], ki, P.kE * n0[j[d]] / P.a3);
+                const double D = limiter_face(P, Ei, E0[j[d]], ki, kappa_start(P, n0, j[d]));
                 w[d] = P.wscale * D;
             }
         }
@@ -96,32 +67,6 @@ __global__ void k_faces(PhysParams P, const double* __restrict__ E0, const doubl
             wzf[i] = (float)w[2];
         }
     }
-}
-
-struct Stencil {
-    long long xm, xp, ym, yp, zm, zp;
-    double wxm, wxp, wym, wyp, wzm, wzp;
-};
-
-__device__ __forceinline__ Stencil stencil(long long i, int x, int y, int z, int nx, int ny, int nz, const int* per,
-                                           const double* __restrict__ wx, const double* __restrict__ wy,
-                                           const double* __restrict__ wz) {
-    Stencil s;
-    const long long sy = nx, sz = (long long)nx * ny;
-    const long long b = i - x - (long long)y * sy - (long long)z * sz;
-    s.xm = b + dn(x, nx, per[0]) + y * sy + z * sz;
-    s.xp = b + up(x, nx, per[0]) + y * sy + z * sz;
-    s.ym = b + x + dn(y, ny, per[1]) * sy + z * sz;
-    s.yp = b + x + up(y, ny, per[1]) * sy + z * sz;
-    s.zm = b + x + y * sy + dn(z, nz, per[2]) * sz;
-    s.zp = b + x + y * sy + up(z, nz, per[2]) * sz;
-    s.wxp = wx[i];
-    s.wyp = wy[i];
-    s.wzp = wz[i];
-    s.wxm = (!per[0] && x == 0) ? 0.0 : wx[s.xm];
-    s.wym = (!per[1] && y == 0) ? 0.0 : wy[s.ym];
-    s.wzm = (!per[2] && z == 0) ? 0.0 : wz[s.zm];
-    return s;
 }
 
 __global__ void k_setup(PhysParams P, const double* __restrict__ E0, const double* __restrict__ n0,
@@ -138,7 +83,7 @@ __global__ void k_setup(PhysParams P, const double* __restrict__ E0, const doubl
         const double E = E0[i];
         const double lap = s.wxp * (E0[s.xp] - E) + s.wxm * (E0[s.xm] - E) + s.wyp * (E0[s.yp] - E) +
                            s.wym * (E0[s.ym] - E) + s.wzp * (E0[s.zp] - E) + s.wzm * (E0[s.zm] - E);
-        const double kap = P.kE * n0[i] / P.a3;
+        const double kap = kappa_start(P, n0, i);
         bE[i] = E + expl * lap + P.dt * (1.0 - P.theta) * (-P.H * E + src[i] - P.c * kap * E);
         const double Ei = E + P.dt * src[i];
         E_init[i] = Ei;

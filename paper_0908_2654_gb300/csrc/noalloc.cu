@@ -60,6 +60,10 @@ extern "C" int rt_residual_static(const rt_grid_desc* desc, const rt_step_inputs
         rt_internal_set_detail("null argument");
         return RT_EINVAL;
     }
+    if (desc->helium) {
+        rt_internal_set_detail("rt_residual_static covers hydrogen-only grids");
+        return RT_EINVAL;
+    }
     const long long n = (long long)desc->nx * desc->ny * desc->nz;
     if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1 || n > kMaxCells) {
         rt_internal_set_detail("rt_residual_static takes at most RT_RESIDUAL_STATIC_MAX_CELLS cells");

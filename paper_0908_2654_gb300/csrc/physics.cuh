@@ -70,7 +70,21 @@ struct PhysParams {
     double src_scale;  // 4 pi eta = src_scale * Ndot in the source's cell
     double alpha_const;
     int isothermal, recomb, cooling, limiter;
+    // hydrogen + helium (helium = 1): mass fraction Y, grey constants of HeI and HeII like kE,
+    // kG, kH, and the step's starting He densities (their opacity enters D^n and b_E)
+    int helium;
+    double Y;
+    double kE1, kE2, kG1, kG2, kH1, kH2;
+    const double* nHeI0;
+    const double* nHeII0;
 };
+
+// proper opacity at the start of the step (hydrogen, plus helium when present)
+RT_HD double kappa_start(const PhysParams& P, const double* n0, long long i) {
+    double k = P.kE * n0[i];
+    if (P.nHeI0) k += P.kE1 * P.nHeI0[i] + P.kE2 * P.nHeII0[i];
+    return k / P.a3;
+}
 
 #define RT_T_HI 157807.0
 #define RT_T_FLOOR 1.0

@@ -52,6 +52,9 @@ class Solver:
         d.T_B = w.get("T_B", 1e5)
         d.recomb = _RECOMB[w["recomb"]]
         d.cooling = 1
+        self.helium = bool(w.get("helium", False))
+        d.helium = int(self.helium)
+        d.Y = float(w.get("Y", 0.0)) if self.helium else 0.0
         d.limiter = _rt.RT_LIMITER_CONST if limiter == "const" else _rt.RT_LIMITER_LAGGED
         d.D_const = D_const
         d.E_min = E_min
@@ -80,7 +83,12 @@ class Solver:
         self.E = dev(w["E"] / u.u_E)
         self.nHI = dev(w["nHI"] / u.u_n)
         self.ec = torch.zeros(self.shape, **f64)
-        e_h = specific_energy(w["T0"], w["rho_b"], w["nHI"], vt)
+        he = None
+        if self.helium:
+            self.nHeI = dev(w["nHeI"] / u.u_n)
+            self.nHeII = dev(w["nHeII"] / u.u_n)
+            he = (w["Y"], w["nHeI"], w["nHeII"])
+        e_h = specific_energy(w["T0"], w["rho_b"], w["nHI"], vt, he)
         self.e_h = dev(e_h / u.u_v**2)
         # time
         cos = w.get("cosmology")
@@ -91,6 +99,8 @@ class Solver:
             self.t = self.cosmo.t_of_z(w["z0"])
             self.dt = ((self.cosmo.t_of_z(w["z_end"]) - self.t) / w["nsteps"]) if "z_end" in w else w["dt"]
         self.stats = []
+        if advect and self.helium:
+            raise ValueError("the advection pre-step covers hydrogen-only grids")
         self.advection = bool(advect)
         self._adv = None
         self.courant = None
@@ -118,11 +128,14 @@ class Solver:
         s.src_ndot = _rt.ptr(self.src_ndot) if s.nsrc else None
         return s
 
-    def state(self, E=None, nHI=None, ec=None):
+    def state(self, E=None, nHI=None, ec=None, nHeI=None, nHeII=None):
         st = _rt.State()
         st.E = _rt.ptr(self.E if E is None else E)
         st.n_HI = _rt.ptr(self.nHI if nHI is None else nHI)
         st.e_c = _rt.ptr(self.ec if ec is None else ec)
+        if self.helium:
+            st.n_HeI = _rt.ptr(self.nHeI if nHeI is None else nHeI)
+            st.n_HeII = _rt.ptr(self.nHeII if nHeII is None else nHeII)
         return st
 
     # ------------------------------------------------------------------- steps
@@ -251,8 +264,27 @@ class Solver:
         return x.cpu().numpy(), its.value
 
     def state_cgs(self):
+        """(e_c, n_HI, E) in CGS; with helium (e_c, n_HI, n_HeI, n_HeII, E)."""
         u = self.units
-        return (self.ec.cpu().numpy() * u.u_v**2, self.nHI.cpu().numpy() * u.u_n, self.E.cpu().numpy() * u.u_E)
+        out = [self.ec.cpu().numpy() * u.u_v**2, self.nHI.cpu().numpy() * u.u_n]
+        if self.helium:
+            out += [self.nHeI.cpu().numpy() * u.u_n, self.nHeII.cpu().numpy() * u.u_n]
+        return tuple(out + [self.E.cpu().numpy() * u.u_E])
+
+    def residual_helium(self, U_n, U, a=None, adot=None):
+        """f(U) (CGS, five components) for a helium grid; U_n = (E, nHI, nHeI, nHeII),
+        U = (e_c, nHI, nHeI, nHeII, E), CGS."""
+        u = self.units
+        En, nn, h1n, h2n = (self.to_device(x, s) for x, s in zip(U_n, (u.u_E, u.u_n, u.u_n, u.u_n)))
+        ec, n, h1, h2, E = (self.to_device(x, s) for x, s in zip(U, (u.u_v**2, u.u_n, u.u_n, u.u_n, u.u_E)))
+        out = [torch.empty_like(E) for _ in range(5)]
+        inp = self.inputs(a, adot)
+        s0 = self.state(En, nn, torch.zeros_like(En), h1n, h2n)
+        s1 = self.state(E, n, ec, h1, h2)
+        _rt.check(_rt.lib().rt_residual_helium(self.handle, ctypes.byref(inp), ctypes.byref(s0), ctypes.byref(s1),
+                                               *[_rt.ptr(t) for t in out]), "rt_residual_helium")
+        scale = (u.u_v**2, u.u_n, u.u_n, u.u_n, u.u_E)
+        return np.stack([t.cpu().numpy() * sc for t, sc in zip(out, scale)])
 
     def grey(self):
         vals = [ctypes.c_double() for _ in range(3)]

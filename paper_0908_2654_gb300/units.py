@@ -43,10 +43,17 @@ class Units:
         return Units(u_x=dx_cm, u_t=u_t, u_g=rho_mean * dx_cm**3)
 
 
-def specific_energy(T, rho_b, nHI, v):
-    """e_h [erg/g] of gas at temperature T with neutral density nHI (X = 1) moving with v."""
-    nH = rho_b / M_H
-    e_int = K_B * T * (2.0 * nH - nHI) / ((GAMMA - 1.0) * rho_b)
+def specific_energy(T, rho_b, nHI, v, helium=None):
+    """e_h [erg/g] of gas at temperature T with neutral density nHI moving with v: hydrogen
+    only (X = 1), or with helium = (Y, n_HeI, n_HeII), where the particle count is
+    n_H + n_He + n_e with n_H = (1 - Y) rho / m_H, n_He = Y rho / (4 m_H)."""
+    if helium is None:
+        n_tot = 2.0 * rho_b / M_H - nHI
+    else:
+        Y, nHeI, nHeII = helium
+        nH, nHe = (1.0 - Y) * rho_b / M_H, 0.25 * Y * rho_b / M_H
+        n_tot = nH + nHe + (nH - nHI) + nHeII + 2.0 * (nHe - nHeI - nHeII)
+    e_int = K_B * T * n_tot / ((GAMMA - 1.0) * rho_b)
     return e_int + 0.5 * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2)
 
 

@@ -3,7 +3,6 @@ case, the species equations of Eq. RT-chemical_ionization) against what fixes th
 series forms of the grey helium constants, adaptive ODE integration of the frozen-coefficient
 rate equations in their unreduced three-species form, equilibrium ratios, the hydrogen-only
 model at Y = 0, helium conservation, and finite differences of the complex-step Jacobian."""
-import dataclasses
 import math
 
 import numpy as np
@@ -94,11 +93,7 @@ def test_hydrogen_with_helium_electrons_matches_ode_integration(A, G, neHe, dt):
 
 def he_step(w):
     """The oracle's hydrogen + helium step for workload w (``workloads.with_helium``)."""
-    base = driver.Run(w).make_step()
-    gh = S.helium_grey_constants(w["spectrum"], w.get("T_B", 1e5))
-    fields = {f.name: getattr(base, f.name) for f in dataclasses.fields(base)}
-    return H.HeStep(**fields, Y=w["Y"], nHeI_n=np.array(w["nHeI"], float), nHeII_n=np.array(w["nHeII"], float),
-                    **gh)
+    return H.Run(w).make_step()
 
 
 def _reion6():
