@@ -154,11 +154,13 @@ def run_gpu(args, rank, world, local_rank):
         barrier()
         torch.cuda.synchronize()
         with ClockSampler(local_rank) as clk:
+            torch.cuda.nvtx.range_push(f"timed_{precision}")   # lets a profiler select these steps
             e0.record(s.stream)
             for _ in range(steps):
                 stats.append(s.step())
             e1.record(s.stream)
             torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
         barrier()
         ms = e0.elapsed_time(e1)
         prof = s.profile() if profile else None
