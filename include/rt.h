@@ -237,8 +237,9 @@ int rt_adjoint_step(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, c
  * the flow leaves moves from one cell to the other.  Moving rho_b with the same fluxes keeps
  * n_HI <= n_H.  The gas energy e_h belongs to the hydrodynamics (pressure work,
  * Eq. enzo-cons_energy) and is not touched.
- * src: E, n_HI read (e_c unused).  dst: E, n_HI written.  rho_src / rho_dst: baryon density in
- * and out (both NULL to leave it alone).  No written array may overlap another argument array.
+ * src: E, n_HI read (e_c unused; on helium grids n_HeI, n_HeII too).  dst: E, n_HI (and the
+ * helium species) written.  rho_src / rho_dst: baryon density in and out (both NULL to leave
+ * it alone).  No written array may overlap another argument array.
  * in->vx, vy, vz: device velocity components in the units of the state (NULL = 0); only
  * in->a, in->dt and the velocities are read from in.
  * courant_max (host pointer, may be NULL) receives the largest per-cell sum of outflow Courant
@@ -251,7 +252,8 @@ int rt_advect(rt_grid* g, const rt_step_inputs* in, const rt_state* src, rt_stat
 /* Transpose of rt_advect's linear map (same inputs), for the adjoint of the operator split:
  * lam_star holds dJ/d(E*, n_HI*) of the advected state, lam receives dJ/d(E, n_HI) before
  * advection (e_c slots unused).  rho_b is not a differentiated variable (it does not depend on
- * the source rates or the clumping factor).  Same argument rules and errors as rt_advect. */
+ * the source rates or the clumping factor).  Hydrogen-only grids (RT_EINVAL with helium).
+ * Same argument rules and errors as rt_advect. */
 int rt_advect_adjoint(rt_grid* g, const rt_step_inputs* in, const rt_state* lam_star, rt_state* lam);
 
 void rt_destroy_grid(rt_grid* g);

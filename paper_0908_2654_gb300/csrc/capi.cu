@@ -525,8 +525,13 @@ AssembleArgs base_args(rt_grid* g, const rt_step_inputs* in) {
 // Courant bound first, so nothing is written when it fails.
 int advect_call(rt_grid* g, const rt_step_inputs* in, const rt_state* src, rt_state* dst, const double* rho_src,
                 double* rho_dst, double* courant_max, bool transpose) {
-    if (g && g->desc.helium) {
-        set_detail("the advection pre-step covers hydrogen-only grids");
+    const bool he = g && g->desc.helium && !transpose;
+    if (g && g->desc.helium && transpose) {
+        set_detail("the adjoint covers hydrogen-only grids");
+        return RT_EINVAL;
+    }
+    if (he && (!src || !dst || !src->n_HeI || !src->n_HeII || !dst->n_HeI || !dst->n_HeII)) {
+        set_detail("helium grid: the advected state needs n_HeI and n_HeII");
         return RT_EINVAL;
     }
     if (!g || !in || !src || !dst || !src->E || !src->n_HI || !dst->E || !dst->n_HI || (!rho_src != !rho_dst)) {
@@ -535,15 +540,15 @@ int advect_call(rt_grid* g, const rt_step_inputs* in, const rt_state* src, rt_st
     }
     const long long n = g->n;
     auto overlaps = [n](const double* a, const double* b) { return a && b && a < b + n && b < a + n; };
-    const double* reads[3] = {src->E, src->n_HI, rho_src};
-    const double* writes[3] = {dst->E, dst->n_HI, rho_dst};
-    for (int w = 0; w < 3; ++w) {
-        for (int r = 0; r < 3; ++r)
+    const double* reads[5] = {src->E, src->n_HI, rho_src, he ? src->n_HeI : nullptr, he ? src->n_HeII : nullptr};
+    const double* writes[5] = {dst->E, dst->n_HI, rho_dst, he ? dst->n_HeI : nullptr, he ? dst->n_HeII : nullptr};
+    for (int w = 0; w < 5; ++w) {
+        for (int r = 0; r < 5; ++r)
             if (overlaps(writes[w], reads[r])) {
                 set_detail("advection source and destination arrays overlap");
                 return RT_EINVAL;
             }
-        for (int w2 = w + 1; w2 < 3; ++w2)
+        for (int w2 = w + 1; w2 < 5; ++w2)
             if (overlaps(writes[w], writes[w2])) {
                 set_detail("advection destination arrays overlap");
                 return RT_EINVAL;
@@ -570,6 +575,12 @@ int advect_call(rt_grid* g, const rt_step_inputs* in, const rt_state* src, rt_st
     A.on = dst->n_HI;
     A.qr = rho_src;
     A.orh = rho_dst;
+    if (he) {
+        A.qh1 = src->n_HeI;
+        A.qh2 = src->n_HeII;
+        A.oh1 = dst->n_HeI;
+        A.oh2 = dst->n_HeII;
+    }
     A.partials = g->partials;
     const double N = (double)n;
     const int nv = (in->vx != nullptr) + (in->vy != nullptr) + (in->vz != nullptr);
@@ -583,7 +594,7 @@ int advect_call(rt_grid* g, const rt_step_inputs* in, const rt_state* src, rt_st
         set_detail("advection Courant number %g exceeds 1", cmax);
         return RT_EINVAL;
     }
-    run(g, K_ADVECT, N * 8.0 * ((rho_src ? 6 : 4) + nv), [&] { launch_advect(A, transpose, g->stream); });
+    run(g, K_ADVECT, N * 8.0 * ((rho_src ? 6 : 4) + (he ? 4 : 0) + nv), [&] { launch_advect(A, transpose, g->stream); });
     if (g->prof_on) {
         RT_CUDA(cudaStreamSynchronize(g->stream));
         harvest(g);

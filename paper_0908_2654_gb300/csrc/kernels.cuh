@@ -104,6 +104,10 @@ struct AdvectArgs {
     double* on;
     const double* qr;      // optional third density moved by the forward map (rho_b), or null
     double* orh;
+    const double* qh1;     // optional helium species moved by the forward map, or null
+    const double* qh2;
+    double* oh1;
+    double* oh2;
     double* partials;      // Courant check: one block maximum per block
 };
 int launch_advect_courant(const AdvectArgs& A, cudaStream_t s);   // returns the number of blocks

@@ -6,7 +6,8 @@
 // zero on a wall face.  The flux c_f q_donor (donor i if c_f > 0, else j) leaves i and enters
 // j.  One thread per cell gathers its six faces; each face is evaluated by both of its cells.
 // The baryon density rho_b (Eq. enzo-cons_mass) can be moved with the same fluxes, which keeps
-// n_HI*/n_H* a convex combination of the neighbours' fractions.  Per cell the forward map reads
+// n_HI*/n_H* a convex combination of the neighbours' fractions; on helium grids n_HeI and
+// n_HeII move with them too.  Per cell the forward map reads
 // E, n_HI, rho_b and three velocity components and writes E*, n_HI*, rho_b* (72 bytes) for
 // about 50 FP64 operations, so on GB300's FP64 pipe it is ALU-bound, not HBM-bound.
 //
@@ -91,6 +92,7 @@ __global__ void __launch_bounds__(kBlock) k_advect(AdvectArgs A) {
         coords(i, A.nx, A.ny, c[0], c[1], c[2]);
         const double Ei = A.qE[i], ni = A.qn[i], ri = A.qr ? A.qr[i] : 0.0;
         double oE = Ei, on = ni, orh = ri;
+        double o1 = A.qh1 ? A.qh1[i] : 0.0, o2 = A.qh2 ? A.qh2[i] : 0.0;
         for (int d = 0; d < 3; ++d) {
             if (!A.v[d]) continue;
             const AxisFaces f = axis_faces(A, d, i, c[d], dims[d], strides[d]);
@@ -99,10 +101,18 @@ __global__ void __launch_bounds__(kBlock) k_advect(AdvectArgs A) {
             oE = oE - (f.cp * A.qE[dp] - f.cm * A.qE[dm]);
             on = on - (f.cp * A.qn[dp] - f.cm * A.qn[dm]);
             if (A.qr) orh = orh - (f.cp * A.qr[dp] - f.cm * A.qr[dm]);
+            if (A.qh1) {
+                o1 = o1 - (f.cp * A.qh1[dp] - f.cm * A.qh1[dm]);
+                o2 = o2 - (f.cp * A.qh2[dp] - f.cm * A.qh2[dm]);
+            }
         }
         A.oE[i] = oE;
         A.on[i] = on;
         if (A.qr) A.orh[i] = orh;
+        if (A.qh1) {
+            A.oh1[i] = o1;
+            A.oh2[i] = o2;
+        }
     }
 }
 

@@ -99,8 +99,6 @@ class Solver:
             self.t = self.cosmo.t_of_z(w["z0"])
             self.dt = ((self.cosmo.t_of_z(w["z_end"]) - self.t) / w["nsteps"]) if "z_end" in w else w["dt"]
         self.stats = []
-        if advect and self.helium:
-            raise ValueError("the advection pre-step covers hydrogen-only grids")
         self.advection = bool(advect)
         self._adv = None
         self.courant = None
@@ -149,9 +147,9 @@ class Solver:
         inp = self.inputs()
         adv = (self.advection if advect is None else advect) and self.has_v
         if adv:
-            E_s, n_s, rho_s = self._advect_to_scratch(inp)
-            inp.rho_b = _rt.ptr(rho_s)
-            st = self.state(E_s, n_s)
+            sc = self._advect_to_scratch(inp)
+            inp.rho_b = _rt.ptr(sc[2])
+            st = self.state(sc[0], sc[1], None, *sc[3:5])
         else:
             st = self.state()
         code = L.rt_implicit_step(self.handle, ctypes.byref(inp), ctypes.byref(st), ctypes.byref(stats))
@@ -160,7 +158,7 @@ class Solver:
             err.stats = stats.as_dict()
             raise err
         if adv:
-            (self.E, self.nHI, self.rho), self._adv = self._adv, (self.E, self.nHI, self.rho)
+            self._swap_advected()
         if fold and not self.w["isothermal"]:
             _rt.check(L.rt_fold_energy(self.handle, _rt.ptr(self.e_h), _rt.ptr(self.ec)), "rt_fold_energy")
         self.t += self.dt
@@ -210,19 +208,27 @@ class Solver:
 
     def _advect_to_scratch(self, inp):
         if self._adv is None:
-            self._adv = tuple(torch.empty_like(self.E) for _ in range(3))
+            self._adv = tuple(torch.empty_like(self.E) for _ in range(5 if self.helium else 3))
         c = ctypes.c_double()
-        src, dst = self.state(), self.state(self._adv[0], self._adv[1])
+        src = self.state()
+        dst = self.state(self._adv[0], self._adv[1], None, *(self._adv[3:5] if self.helium else ()))
         _rt.check(_rt.lib().rt_advect(self.handle, ctypes.byref(inp), ctypes.byref(src), ctypes.byref(dst),
                                       _rt.ptr(self.rho), _rt.ptr(self._adv[2]), ctypes.byref(c)), "rt_advect")
         self.courant = c.value
         return self._adv
 
+    def _swap_advected(self):
+        cur = (self.E, self.nHI, self.rho) + ((self.nHeI, self.nHeII) if self.helium else ())
+        self.E, self.nHI, self.rho = self._adv[:3]
+        if self.helium:
+            self.nHeI, self.nHeII = self._adv[3:5]
+        self._adv = cur
+
     def advect(self):
-        """Advection pre-step (step (iv) for rho_b, n_HI and E, donor cell) over this step's
-        dt, in place; returns the largest Courant number."""
+        """Advection pre-step (step (iv) for rho_b, n_HI, E and the helium species, donor
+        cell) over this step's dt, in place; returns the largest Courant number."""
         self._advect_to_scratch(self.inputs())
-        (self.E, self.nHI, self.rho), self._adv = self._adv, (self.E, self.nHI, self.rho)
+        self._swap_advected()
         return self.courant
 
     # ---------------------------------------------------------- kernel access

@@ -165,3 +165,24 @@ def test_gradients_through_advection_match_oracle_dense_adjoint():
     np.testing.assert_allclose(ndot.grad.cpu().numpy(), go_ndot, rtol=1e-6)
     g = clump.grad.cpu().numpy()
     assert np.max(np.abs(g - go_clump)) <= 1e-6 * np.abs(go_clump).max()
+
+
+def test_helium_species_move_with_the_same_fluxes():
+    """On a helium grid n_HeI and n_HeII are advected like n_HI (oracle scheme, field by field),
+    and stay within n_He of the advected density."""
+    from paper_0908_2654_gb300 import _rt
+    w = W.with_helium(W.random_state((8, 6, 10), seed=21, periodic=(True, False, True)))
+    s = _solver(w)
+    a = _scale_dt(s, w, 0.9)
+    u = s.units
+    out = [torch.empty_like(s.E) for _ in range(5)]
+    dst = s.state(out[0], out[1], None, out[3], out[4])
+    code, _ = _advect(s, s.state(), dst, rho=(s.rho, out[2]))
+    _rt.check(code, "rt_advect")
+    args = (w["v"], a, s.dt, w["dx"], w["periodic"])
+    for got, q, scale in ((out[3], w["nHeI"], u.u_n), (out[4], w["nHeII"], u.u_n), (out[1], w["nHI"], u.u_n)):
+        ref = ADV.advect(q, *args)
+        assert np.max(np.abs(got.cpu().numpy() * scale - ref)) < TOL * np.max(np.abs(ref))
+    nHe = 0.25 * w["Y"] * out[2]
+    assert torch.all(out[3] + out[4] <= nHe * (1 + 1e-12)) and torch.all(out[3] >= 0) and torch.all(out[4] >= 0)
+    s.close()
