@@ -122,6 +122,25 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ----------------------------------------------------------- whole-job numbers
+
+
+def reduce_max(value, world, device):
+    """Largest value over the ranks: the job takes as long as its slowest replica."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, cells, steps, ms_max):
+    """Cell-steps per second of the whole job: every replica advances its own grid."""
+    return world * cells * steps / (ms_max * 1e-3)
+
+
 # -------------------------------------------------------------------- GPU arm
 
 
@@ -168,20 +187,15 @@ def run_gpu(args, rank, world, local_rank):
         return ms, stats, prof, clk.summary()
 
     ms_mixed, st_mixed, prof, clocks = timed("mixed", args.steps, args.warmup, profile=True)
-    t = torch.tensor([ms_mixed], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * cells * args.steps / (ms_max * 1e-3)
+    ms_max = reduce_max(ms_mixed, world, dev)
+    value = job_rate(world, cells, args.steps, ms_max)
 
     fp64 = None
     if not args.no_fp64:
         ms64, st64, _, _ = timed("fp64", args.steps, args.warmup, profile=False)
-        t = torch.tensor([ms64], device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        v64 = world * cells * args.steps / (float(t.item()) * 1e-3)
-        fp64 = {"value": v64, "ms_per_step": float(t.item()) / args.steps,
+        ms64 = reduce_max(ms64, world, dev)
+        v64 = job_rate(world, cells, args.steps, ms64)
+        fp64 = {"value": v64, "ms_per_step": ms64 / args.steps,
                 "newton_iters": [x["newton_iters"] for x in st64], "linear_iters": [x["linear_iters"] for x in st64],
                 "speedup_mixed_vs_fp64": value / v64}
 
@@ -253,10 +267,10 @@ def run_e2e(args, w, local_rank, barrier, world):
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1)
+    ms = reduce_max(e0.elapsed_time(e1), world, torch.device("cuda", local_rank))
     s.close()
     cells = w["nx"] * w["ny"] * w["nz"]
-    return {"value": world * cells * args.steps / (ms * 1e-3), "unit": "cell-steps/s",
+    return {"value": job_rate(world, cells, args.steps, ms), "unit": "cell-steps/s",
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
 
 
