@@ -122,6 +122,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------ mixed against FP64 final states
+
+
+def _final_state(s):
+    """(E, x_HI, T) of a solver's current state on the host (CGS E, temperature in K)."""
+    from paper_0908_2654_gb300.units import temperature
+    ec, nHI, E = s.state_cgs()
+    u = s.units
+    rho = s.rho.cpu().numpy() * u.u_d
+    v = tuple(x.cpu().numpy() * u.u_v for x in s.v)
+    T = temperature(s.e_h.cpu().numpy() * u.u_v**2, rho, nHI, v)
+    return E, nHI / (rho / 1.6735575e-24), T
+
+
+def state_errors(a, b):
+    """Differences of state a from the reference b: E normwise (2 and max, relative), x_HI and T
+    pointwise relative (x_HI with a floor of 1e-8)."""
+    Ea, xa, Ta = a
+    Eb, xb, Tb = b
+    return {"E_rel_2": float(np.linalg.norm(Ea - Eb) / np.linalg.norm(Eb)),
+            "E_rel_inf": float(np.max(np.abs(Ea - Eb)) / np.max(np.abs(Eb))),
+            "xHI_rel_max": float(np.max(np.abs(xa - xb) / np.maximum(xb, 1e-8))),
+            "T_rel_max": float(np.max(np.abs(Ta - Tb) / Tb))}
+
+
 # ----------------------------------------------------------- whole-job numbers
 
 
@@ -183,21 +208,23 @@ def run_gpu(args, rank, world, local_rank):
         barrier()
         ms = e0.elapsed_time(e1)
         prof = s.profile() if profile else None
+        final = _final_state(s)
         s.close()
-        return ms, stats, prof, clk.summary()
+        return ms, stats, prof, clk.summary(), final
 
-    ms_mixed, st_mixed, prof, clocks = timed("mixed", args.steps, args.warmup, profile=True)
+    ms_mixed, st_mixed, prof, clocks, final_mixed = timed("mixed", args.steps, args.warmup, profile=True)
     ms_max = reduce_max(ms_mixed, world, dev)
     value = job_rate(world, cells, args.steps, ms_max)
 
     fp64 = None
     if not args.no_fp64:
-        ms64, st64, _, _ = timed("fp64", args.steps, args.warmup, profile=False)
+        ms64, st64, _, _, final64 = timed("fp64", args.steps, args.warmup, profile=False)
         ms64 = reduce_max(ms64, world, dev)
         v64 = job_rate(world, cells, args.steps, ms64)
         fp64 = {"value": v64, "ms_per_step": ms64 / args.steps,
                 "newton_iters": [x["newton_iters"] for x in st64], "linear_iters": [x["linear_iters"] for x in st64],
-                "speedup_mixed_vs_fp64": value / v64}
+                "speedup_mixed_vs_fp64": value / v64,
+                "mixed_vs_fp64_error": state_errors(final_mixed, final64)}
 
     advect = None if args.no_advect else run_advect(w, local_rank)
 
