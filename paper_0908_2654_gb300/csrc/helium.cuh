@@ -16,8 +16,9 @@
 //    frozen, x' = M x + c: x = x_ss + e^{M dt}(x0 - x_ss) with the steady state x_ss and
 //    e^{M dt} = c1 I + s (M - mu I) from M's real eigenvalues mu +- delta (the chain is a
 //    birth-death process), c1 = (e^{mu1 dt} + e^{mu2 dt})/2 and s = (e^{mu1 dt} - e^{mu2 dt}) /
-//    (2 delta), the difference taken as e^{mu2 dt} expm1(z) for z = 2 delta dt < 1; when every
-//    rate times dt is below 1e-8 a second-order Taylor step.
+//    (mu1 - mu2), the difference taken as e^{mu2 dt} expm1(z) for z = 2 delta dt < 1 and the
+//    slow eigenvalue as det(M) / mu2 otherwise; when |tr M| dt < 1e-3 (where x_ss and
+//    e^{M dt} would cancel) the Taylor series of the solution to (M dt)^5 instead.
 #pragma once
 #include "physics.cuh"
 
@@ -115,11 +116,21 @@ RT_HD void helium_chain(double x10, double x20, double nHe, const T& G1, const T
     const T c2 = r3 * nHe;
     const T tr = M11 + M22;
     const T det = G1 * G2 + G1 * r3 + r2 * r3;
-    if (fabs(value(tr)) * dt < 1e-8 || !(value(det) > 0.0)) {
+    if (fabs(value(tr)) * dt < 1e-3 || !(value(det) > 0.0)) {
+        // x = x0 + dt sum_{j<5} (M dt)^j / (j+1)! (M x0 + c), by Horner; every entry of M is
+        // at most |tr M|, so the first omitted term is below (2e-3)^6 / 720 relative
         const T v1 = M11 * x10 + M12 * x20, v2 = M21 * x10 + M22 * x20 + c2;
-        const T w1 = M11 * v1 + M12 * v2, w2 = M21 * v1 + M22 * v2;
-        x1 = x10 + dt * v1 + (0.5 * dt * dt) * w1;
-        x2 = x20 + dt * v2 + (0.5 * dt * dt) * w2;
+        T u1 = v1, u2 = v2;
+#pragma unroll
+        for (int k = 5; k >= 2; --k) {
+            const double f = dt / k;
+            const T t1 = v1 + f * (M11 * u1 + M12 * u2);
+            const T t2 = v2 + f * (M21 * u1 + M22 * u2);
+            u1 = t1;
+            u2 = t2;
+        }
+        x1 = x10 + dt * u1;
+        x2 = x20 + dt * u2;
         return;
     }
     const T fss = c2 / det;
@@ -136,9 +147,12 @@ RT_HD void helium_chain(double x10, double x20, double nHe, const T& G1, const T
         const T phe = (value(z) < 1e-8) ? 1.0 + z * 0.5 + z * z * (1.0 / 6.0) : expm1(z) / z;
         s = E2 * (dt * phe);
         c1 = E2 + 0.5 * (E2 * z * phe);
-    } else {                        // both exponentials directly (mu1, mu2 <= 0: no overflow)
-        const T E1 = fexp((mu + delta) * dt);
-        s = (E1 - E2) / (2.0 * delta);
+    } else {                        // both exponentials directly (mu1, mu2 <= 0: no overflow);
+        // the slow eigenvalue as det / mu2 (mu + delta cancels when one rate dominates)
+        const T mu2 = mu - delta;
+        const T mu1 = det / mu2;
+        const T E1 = fexp(mu1 * dt);
+        s = (E1 - E2) / (mu1 - mu2);
         c1 = 0.5 * (E1 + E2);
     }
     const T y1 = x10 - s1, y2 = x20 - s2;

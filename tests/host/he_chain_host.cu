@@ -1,0 +1,28 @@
+// Host build of the GPU path's helium chain and hydrogen-with-helium-electrons Riccati solution
+// (helium.cuh, compiled for the CPU) so that tests can compare them with the oracle across
+// parameter regimes; derivatives through the same dual numbers the kernels use.
+#include "../../paper_0908_2654_gb300/csrc/helium.cuh"
+
+extern "C" {
+
+// x1, x2 = helium_chain at each of n parameter sets; d1, d2 = their derivatives in G1 and r3
+void he_chain_host(int n, const double* x10, const double* x20, const double* nHe, const double* G1,
+                   const double* G2, const double* r2, const double* r3, const double* dt, double* x1, double* x2,
+                   double* dx1_dG1, double* dx2_dr3) {
+    for (int i = 0; i < n; ++i) {
+        Dual<2> a, b;
+        helium_chain<Dual<2>>(x10[i], x20[i], nHe[i], dvar<2>(G1[i], 0), dconst<2>(G2[i]), dconst<2>(r2[i]),
+                              dvar<2>(r3[i], 1), dt[i], a, b);
+        x1[i] = a.v;
+        x2[i] = b.v;
+        dx1_dG1[i] = a.d[0];
+        dx2_dr3[i] = b.d[1];
+    }
+}
+
+void riccati_ne_host(int n, const double* y0, const double* nH, const double* neHe, const double* A,
+                     const double* G, const double* dt, double* y) {
+    for (int i = 0; i < n; ++i) y[i] = riccati_ne<double>(y0[i], nH[i], neHe[i], A[i], G[i], dt[i]);
+}
+
+}

@@ -1,0 +1,99 @@
+"""The GPU path's closed forms for helium (helium.cuh: the helium chain from the real
+eigenvalues of its rate matrix, with its Taylor and large-eigenvalue-gap branches, and the
+hydrogen Riccati solution with helium electrons), compiled for the host, against the oracle's
+independent routes (expm of the augmented matrix; the oracle's Riccati form) across stiff,
+slow, degenerate and strongly driven regimes, values and derivatives."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import helium as H
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def host_lib(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    out = str(tmp_path_factory.mktemp("host") / "he_chain_host.so")
+    subprocess.run([nvcc, "-x", "cu", "-std=c++17", "--expt-relaxed-constexpr", "-O2", "-shared", "-Xcompiler",
+                    "-fPIC", "-gencode", "arch=compute_103a,code=sm_103a", os.path.join(HERE, "host", "he_chain_host.cu"),
+                    "-o", out], check=True, capture_output=True)
+    return ctypes.CDLL(out)
+
+
+def _arr(x):
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _regimes(rng, n):
+    """Rate sets in 1/s over 10 decades, with zero photo-ionisation, zero electrons, equal
+    recombination rates (coincident eigenvalues) and strongly driven cells among them."""
+    G1 = 10 ** rng.uniform(-20, -9, n)
+    G2 = G1 * 10 ** rng.uniform(-3, 0, n)
+    r2 = 10 ** rng.uniform(-20, -11, n)
+    r3 = r2 * 10 ** rng.uniform(-1, 1.5, n)
+    dt = 10 ** rng.uniform(10, 15, n)
+    k = n // 8
+    G1[:k] = G2[:k] = 0.0                       # recombination only
+    r2[k:2 * k] = r3[k:2 * k] = 0.0             # no electrons
+    r3[2 * k:3 * k] = r2[2 * k:3 * k]           # coincident eigenvalues
+    G1[3 * k:4 * k] *= 1e4                      # strongly driven (large 2 delta dt)
+    return G1, G2, r2, r3, dt
+
+
+def test_helium_chain_matches_oracle(host_lib):
+    rng = np.random.default_rng(11)
+    n = 4000
+    G1, G2, r2, r3, dt = _regimes(rng, n)
+    nHe = np.ones(n)
+    f1 = rng.uniform(0, 1, n)
+    x10 = f1 * rng.uniform(0, 1, n)
+    x20 = (1 - f1) * rng.uniform(0, 1, n)
+    out = [np.empty(n) for _ in range(4)]
+    args = [_arr(v) for v in (x10, x20, nHe, G1, G2, r2, r3, dt)]
+    host_lib.he_chain_host(ctypes.c_int(n), *[_p(a) for a in args], *[_p(o) for o in out])
+    x1, x2, d1, d2 = out
+    # the oracle's chain takes one dt; the solution depends on the rates only through rate * dt
+    ref1, ref2 = (np.real(v) for v in H.he_chain((x10, x20), nHe, G1 * dt, G2 * dt, r2 * dt, r3 * dt, 1.0))
+    # scaling and squaring in the oracle's expm loses ~1e-11 at |M dt| ~ 1e7 (the closed form
+    # matches a 50-digit evaluation to 1e-16 there)
+    assert np.max(np.abs(x1 - ref1)) < 1e-10
+    assert np.max(np.abs(x2 - ref2)) < 1e-10
+    # derivatives in G1 and r3 against complex steps through the oracle's route
+    h = 1e-30
+    g1 = (G1 + 1j * h * np.maximum(G1, 1e-25)) * dt
+    c1 = np.imag(H.he_chain((x10, x20), nHe, g1, G2 * dt, r2 * dt, r3 * dt, 1.0)[0]) / (h * np.maximum(G1, 1e-25))
+    g3 = (r3 + 1j * h * np.maximum(r3, 1e-25)) * dt
+    c2 = np.imag(H.he_chain((x10, x20), nHe, G1 * dt, G2 * dt, r2 * dt, g3, 1.0)[1]) / (h * np.maximum(r3, 1e-25))
+    s1 = np.maximum(np.abs(c1), 1e-300) * 1e-7 + 1e-9 * dt
+    s2 = np.maximum(np.abs(c2), 1e-300) * 1e-7 + 1e-9 * dt
+    assert np.all(np.abs(d1 - c1) <= s1)
+    assert np.all(np.abs(d2 - c2) <= s2)
+
+
+def test_hydrogen_with_helium_electrons_matches_oracle(host_lib):
+    rng = np.random.default_rng(12)
+    n = 2000
+    nH = np.ones(n)
+    y0 = rng.uniform(1e-6, 1.0, n)
+    neHe = rng.uniform(0.0, 0.2, n)
+    A = 10 ** rng.uniform(-20, -12, n)
+    G = 10 ** rng.uniform(-22, -10, n)
+    G[: n // 10] = 0.0
+    dt = 10 ** rng.uniform(10, 15, n)
+    y = np.empty(n)
+    args = [_arr(v) for v in (y0, nH, neHe, A, G, dt)]
+    host_lib.riccati_ne_host(ctypes.c_int(n), *[_p(a) for a in args], _p(y))
+    ref = np.real(H.riccati_SHI(y0, nH, neHe, A, G, dt))
+    assert np.max(np.abs(y - ref)) < 1e-12
