@@ -1,6 +1,8 @@
 // Host build of the GPU path's helium chain and hydrogen-with-helium-electrons Riccati solution
 // (helium.cuh, compiled for the CPU) so that tests can compare them with the oracle across
 // parameter regimes; derivatives through the same dual numbers the kernels use.
+#include <cstring>
+
 #include "../../paper_0908_2654_gb300/csrc/helium.cuh"
 
 extern "C" {
@@ -23,6 +25,28 @@ void he_chain_host(int n, const double* x10, const double* x20, const double* nH
 void riccati_ne_host(int n, const double* y0, const double* nH, const double* neHe, const double* A,
                      const double* G, const double* dt, double* y) {
     for (int i = 0; i < n; ++i) y[i] = riccati_ne<double>(y0[i], nH[i], neHe[i], A[i], G[i], dt[i]);
+}
+
+}
+
+extern "C" {
+
+// rate fits of the GPU path at n temperatures (recomb = 1: Hui & Gnedin hydrogen alpha), with
+// d/dT of each from the single-lane promotion the kernels use; outputs [9][n]:
+// alpha_H, alpha_HeII(+di), alpha_HeIII, rec+ff, ff, ce, comp, c2, c3 (and the same for d/dT)
+void rates_host(int n, const double* T, double a, double* out, double* dout) {
+    PhysParams P;
+    memset(&P, 0, sizeof(P));
+    P.recomb = 1;
+    P.a = a;
+    for (int i = 0; i < n; ++i) {
+        const HeRates<Dual<1>> r = he_rates<1>(P, dvar<1>(T[i], 0), true);
+        const Dual<1>* v[9] = {&r.aH, &r.a2, &r.a3, &r.rf, &r.ff, &r.ce, &r.comp, &r.c2, &r.c3};
+        for (int k = 0; k < 9; ++k) {
+            out[k * n + i] = v[k]->v;
+            dout[k * n + i] = v[k]->d[0];
+        }
+    }
 }
 
 }

@@ -97,3 +97,39 @@ def test_hydrogen_with_helium_electrons_matches_oracle(host_lib):
     host_lib.riccati_ne_host(ctypes.c_int(n), *[_p(a) for a in args], _p(y))
     ref = np.real(H.riccati_SHI(y0, nH, neHe, A, G, dt))
     assert np.max(np.abs(y - ref)) < 1e-12
+
+
+def test_rate_fits_match_oracle_over_temperature(host_lib):
+    """Hydrogen and helium recombination coefficients and the cooling coefficients of the GPU
+    path (one d/dT lane, chained) against the oracle's rate functions from 1 K to 1e9 K; the
+    cooling coefficients are compared through the oracle's total cooling with one density at
+    a time switched on."""
+    from oracle import constants as K
+    from oracle import rates as R
+    n = 400
+    T = np.logspace(0, 9, n)
+    a = 0.1
+    out, dout = np.empty(9 * n), np.empty(9 * n)
+    host_lib.rates_host(ctypes.c_int(n), _p(_arr(T)), ctypes.c_double(a), _p(out), _p(dout))
+    out, dout = out.reshape(9, n), dout.reshape(9, n)
+    aH, a2, a3, rf, ff, ce, comp, c2, c3 = out
+    np.testing.assert_allclose(aH, R.alpha_B(T, "hg97"), rtol=1e-13)
+    np.testing.assert_allclose(a2, R.alpha_HeII_B(T) + R.alpha_di(T), rtol=1e-13)
+    np.testing.assert_allclose(a3, R.alpha_HeIII_B(T), rtol=1e-13)
+    one, zero = np.ones(n), np.zeros(n)
+    # cooling_rate_he(T, n_e, n_HI, n_HII, n_HeII, n_HeIII, a) with n_e = 1 and one other density
+    cool = lambda nHI, nHII, n2, n3: R.cooling_rate_he(T, one, nHI, nHII, n2, n3, a)
+    comp_ref = cool(zero, zero, zero, zero)
+    np.testing.assert_allclose(comp, comp_ref, rtol=1e-12, atol=1e-40)
+    # each reference is (total - Compton): its rounding is of the size of the Compton term
+    ac = 1e-14 * np.abs(comp_ref)
+    np.testing.assert_allclose(rf, cool(zero, one, zero, zero) - comp_ref, rtol=1e-12, atol=ac.max())
+    np.testing.assert_allclose(ce, cool(one, zero, zero, zero) - comp_ref, rtol=1e-11, atol=ac.max())
+    np.testing.assert_allclose(ff + c2, cool(zero, zero, one, zero) - comp_ref, rtol=1e-11, atol=ac.max())
+    np.testing.assert_allclose(4 * ff + c3, cool(zero, zero, zero, one) - comp_ref, rtol=1e-11, atol=ac.max())
+    # d/dT of the recombination coefficients against complex steps of the oracle's fits
+    h = 1e-20
+    for got, f in ((dout[0], lambda t: R.alpha_B(t, "hg97")), (dout[1], lambda t: R.alpha_HeII_B(t) + R.alpha_di(t)),
+                   (dout[2], R.alpha_HeIII_B)):
+        ref = np.imag(f(T + 1j * h * T)) / (h * T)
+        np.testing.assert_allclose(got, ref, rtol=1e-10, atol=1e-300)
