@@ -50,3 +50,13 @@ void rates_host(int n, const double* T, double a, double* out, double* dout) {
 }
 
 }
+
+extern "C" {
+
+// hydrogen-only Riccati solution of the GPU path (shared expm1 decay factors)
+void riccati_n_host(int n, const double* y0, const double* nH, const double* A, const double* G, const double* dt,
+                    double* y) {
+    for (int i = 0; i < n; ++i) y[i] = riccati_n<double>(y0[i], nH[i], A[i], G[i], dt[i]);
+}
+
+}

@@ -133,3 +133,22 @@ def test_rate_fits_match_oracle_over_temperature(host_lib):
                    (dout[2], R.alpha_HeIII_B)):
         ref = np.imag(f(T + 1j * h * T)) / (h * T)
         np.testing.assert_allclose(got, ref, rtol=1e-10, atol=1e-300)
+
+
+def test_hydrogen_riccati_matches_oracle(host_lib):
+    """S_n of the hydrogen-only path (e^-x and phi1 from one expm1, with the series below
+    |x| = 1e-8) against the oracle's form, from frozen chemistry (d dt ~ 1e-12) to stiff."""
+    from oracle import model as M
+    rng = np.random.default_rng(13)
+    n = 3000
+    nH = np.ones(n)
+    y0 = rng.uniform(1e-6, 1.0, n)
+    A = 10 ** rng.uniform(-24, -10, n)
+    G = 10 ** rng.uniform(-26, -8, n)
+    G[: n // 10] = 0.0
+    dt = 10 ** rng.uniform(10, 15, n)
+    y = np.empty(n)
+    args = [_arr(v) for v in (y0, nH, A, G, dt)]
+    host_lib.riccati_n_host(ctypes.c_int(n), *[_p(a) for a in args], _p(y))
+    ref = np.real(M.riccati_Sn(y0, nH, A, G, dt))
+    assert np.max(np.abs(y - ref)) < 1e-13
