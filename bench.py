@@ -372,22 +372,9 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def main():
-    args = parse()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        if rank == 0:
-            run_reference(args)
-        return
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    res = run_gpu(args, rank, world, local_rank)
-    if rank != 0:
-        return
-    peaks = load_peaks()
+def bench_line(args, res, world, peaks):
+    """The JSON line of the GPU arm from run_gpu's results (rooflines from the per-kernel
+    profile, kernel table, launch count)."""
     prof = res["prof"] or {}
     dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
     roof = None
@@ -414,8 +401,16 @@ def main():
                     "flops_per_cell": ASSEMBLE_FP64_FLOPS_PER_CELL, "share_of_step": dom["ms"] / res["ms"]}
         else:
             roof = hbm_roof(dom_name, dom)
-    smooth = prof.get("mg_rbgs")
-    roof_mg = hbm_roof("mg_rbgs", smooth) if smooth else None
+    # the smoother over all levels, and its fine-level passes alone (the coarse levels are a few
+    # microseconds each and latency-bound)
+    parts = [prof[k] for k in ("mg_rbgs", "mg_rbgs_fine") if k in prof]
+    roof_mg = None
+    if parts:
+        smooth = {key: sum(p[key] for p in parts) for key in ("launches", "ms", "bytes")}
+        roof_mg = hbm_roof("mg_rbgs", smooth)
+        if "mg_rbgs_fine" in prof:
+            fine = hbm_roof("mg_rbgs_fine", prof["mg_rbgs_fine"])
+            roof_mg["fine_level"] = {k: fine[k] for k in ("achieved", "frac", "share_of_step")}
     roof_adv = None
     if res["advect"] and "advect" in res["advect"]:
         v = res["advect"]["advect"]
@@ -450,6 +445,25 @@ def main():
         "clocks": res["clocks"],
         "e2e": res["e2e"],
     }
+    return line
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res = run_gpu(args, rank, world, local_rank)
+    if rank != 0:
+        return
+    line = bench_line(args, res, world, load_peaks())
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(res["w"], args.newton_tol)
     print(json.dumps(line))

@@ -202,13 +202,13 @@ int check_launch(const char* what) {
 enum KClass {
     K_ZERO, K_SOURCES, K_FACES, K_SETUP, K_ASSEMBLE, K_FINALIZE, K_SPMV, K_RESNORM, K_CG_UPDATE, K_DOT2, K_P_UPDATE,
     K_SCALARS, K_COPY, K_CAST, K_MG_DIAG, K_COARSEN, K_RBGS, K_RESTRICT, K_PROLONG, K_TAIL, K_ADD, K_ADVECT,
-    K_ADVECT_CHECK, K_NCLASS
+    K_ADVECT_CHECK, K_RBGS_FINE, K_NCLASS
 };
 const char* kClassName[K_NCLASS] = {"zero", "scatter_sources", "faces", "setup", "newton_assemble", "finalize",
                                     "cg_spmv_dot", "cg_residual", "cg_update_xr", "cg_dot2", "cg_p_update",
                                     "cg_scalars", "copy", "cast", "mg_diag", "mg_coarsen", "mg_rbgs",
                                     "mg_resid_restrict", "mg_prolong_add", "mg_coarse_cta", "add", "advect",
-                                    "advect_courant"};
+                                    "advect_courant", "mg_rbgs_fine"};
 
 // Launch f() as kernel class cls moving `bytes` algorithmic bytes; brackets it with events
 // when profiling is on.
@@ -308,9 +308,10 @@ void vcycle(rt_grid* g, Hierarchy<T>& H) {
     const double rb = 5.5 * t;
     for (int l = 0; l < last; ++l) {
         const double n = (double)H.lv[l].d.n();
+        const int cls = l == 0 ? K_RBGS_FINE : K_RBGS;   // the fine level timed on its own
         for (int k = 0; k < nu1; ++k) {
-            run(g, K_RBGS, n * rb, [&] { launch_rbgs<T>(H.lv[l], 0, k == 0, s); });
-            run(g, K_RBGS, n * rb, [&] { launch_rbgs<T>(H.lv[l], 1, false, s); });
+            run(g, cls, n * rb, [&] { launch_rbgs<T>(H.lv[l], 0, k == 0, s); });
+            run(g, cls, n * rb, [&] { launch_rbgs<T>(H.lv[l], 1, false, s); });
         }
         run(g, K_RESTRICT, n * 6.125 * t, [&] { launch_resid_restrict<T>(H.lv[l], H.lv[l + 1], s); });
     }
@@ -318,9 +319,10 @@ void vcycle(rt_grid* g, Hierarchy<T>& H) {
     for (int l = last - 1; l >= 0; --l) {
         const double n = (double)H.lv[l].d.n();
         run(g, K_PROLONG, n * 2.125 * t, [&] { launch_prolong_add<T>(H.lv[l + 1], H.lv[l], s); });
+        const int cls = l == 0 ? K_RBGS_FINE : K_RBGS;
         for (int k = 0; k < nu2; ++k) {
-            run(g, K_RBGS, n * rb, [&] { launch_rbgs<T>(H.lv[l], 1, false, s); });
-            run(g, K_RBGS, n * rb, [&] { launch_rbgs<T>(H.lv[l], 0, false, s); });
+            run(g, cls, n * rb, [&] { launch_rbgs<T>(H.lv[l], 1, false, s); });
+            run(g, cls, n * rb, [&] { launch_rbgs<T>(H.lv[l], 0, false, s); });
         }
     }
 }

@@ -1,0 +1,43 @@
+"""bench.py's JSON line assembled from fake GPU results on the CPU: every key the output
+contract asks for, the roofline arithmetic of the dominant kernel and of the smoother (all
+levels and the fine level alone), and that the line serialises."""
+import argparse
+import json
+
+import pytest
+
+import bench
+
+
+def _res():
+    prof = {
+        "newton_assemble": dict(launches=20, ms=700.0, bytes=20 * 212.0 * 256**3),
+        "mg_rbgs": dict(launches=6000, ms=60.0, bytes=3.0e11),
+        "mg_rbgs_fine": dict(launches=2000, ms=180.0, bytes=7.0e11),
+        "cg_spmv_dot": dict(launches=140, ms=37.0, bytes=1.1e11),
+    }
+    stats = [dict(newton_iters=4, linear_iters=35, kernel_launches=2970) for _ in range(4)]
+    return dict(value=5.6e7, ms=1190.0, stats=stats, prof=prof, fp64={"value": 4.1e7},
+                clocks={"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []},
+                e2e={"value": 5.1e7, "unit": "cell-steps/s", "h2d_bytes_per_step": 1, "d2h_bytes_per_step": 1},
+                w=None, advect={"advect": dict(launches=10, ms=16.3, bytes=10 * 72.0 * 256**3), "courant_max": 0.05})
+
+
+def test_bench_line_contract_and_rooflines():
+    args = argparse.Namespace(size=256, steps=4, warmup=3, newton_tol=1e-6, lin_rtol=1e-3)
+    line = bench.bench_line(args, _res(), 1, {"hbm_gbs": 6797.2})
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "gpu_launches", "clocks", "e2e"):
+        assert key in line, key
+    roof = line["roofline"]
+    assert roof["kernel"] == "newton_assemble" and roof["bound"] == "alu"
+    assert roof["achieved"] == pytest.approx(bench.ASSEMBLE_FP64_FLOPS_PER_CELL * 256**3 / 0.035 / 1e12)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
+    assert roof["traffic"] == pytest.approx(bench.ASSEMBLE_DRAM_BYTES_PER_CELL * 256**3)
+    mg = line["roofline_vcycle_smoother"]
+    assert mg["achieved"] == pytest.approx(1.0e12 / 8000 / (0.24 / 8000) / 1e9)          # all levels
+    assert mg["fine_level"]["achieved"] == pytest.approx(7.0e11 / 0.180 / 1e9)
+    assert mg["fine_level"]["frac"] == pytest.approx(mg["fine_level"]["achieved"] / 6797.2)
+    assert line["gpu_launches"] == 4 * 2970 + 4
+    assert line["ms_per_step"] == pytest.approx(1190.0 / 4)
+    json.loads(json.dumps(line))
