@@ -1,4 +1,4 @@
-"""Rate coefficients for hydrogen-only gas (oracle; test infrastructure only).
+"""Rate coefficients for hydrogen and hydrogen + helium gas (oracle; test infrastructure only).
 
 Sec. "Physical Model": G, Lambda, alpha_ij and Gamma^ph are functions of T, E and
 the ionisation state, with formulas the paper cites but does not print.  Readings
@@ -13,9 +13,14 @@ used (identical in the CUDA library, written there independently):
   off the CMB (4 k_B sigma_T a_rad T_cmb^4 (T - T_cmb) n_e / (m_e c)).
   Collisional ionisation is not included.
 
-Pins: alpha_hg97(1e4 K) reproduces the paper's 2.59e-13 to 0.1 %.  The cooling
-functions and the shape of alpha_hg97 away from 1e4 K are parity unpinned
-(no printed value in the paper; implementation-against-implementation only).
+Pins: alpha_hg97(1e4 K) reproduces the paper's 2.59e-13 to 0.1 %.  The paper prints
+no other rate value; the fits are pinned instead to facts of atomic physics that do not
+depend on them (tests/test_oracle_rate_pins.py): textbook case-B coefficients, the
+hydrogenic scaling of recombination and its cooling to Z = 2, the bound of 3/2 kT on the
+mean energy a recombination removes, the Kramers-Gaunt bremsstrahlung coefficient from
+fundamental constants, the Lyman-alpha energies in the excitation exponents, Cen's Compton
+coefficient.  Parity unpinned: the shapes of the Gaunt factor, of the excitation prefactors
+and of the HeI recombination fit.
 
 All functions accept complex arguments (the oracle Jacobian uses complex steps).
 """
@@ -41,19 +46,6 @@ def alpha_B(T, mode):
     return 2.753e-14 * lam**1.5 / (1.0 + (lam / 2.740) ** 0.407) ** 2.242
 
 
-def cooling_rate(T, n_e, n_HI, n_HII, a):
-    """Total cooling Lambda per unit proper volume [erg cm^-3 s^-1] (proper densities)."""
-    T = _cmax(T, T_FLOOR)
-    lam = 2.0 * T_HI / T
-    rec = 3.435e-30 * T * lam**1.970 / (1.0 + (lam / 2.250) ** 0.376) ** 3.720 * n_e * n_HII
-    ce = 7.5e-19 * np.exp(-118348.0 / T) / (1.0 + np.sqrt(T / 1e5)) * n_e * n_HI
-    gff = 1.1 + 0.34 * np.exp(-((5.5 - np.log10(T)) ** 2) / 3.0)
-    ff = 1.42e-27 * gff * np.sqrt(T) * n_e * n_HII
-    T_cmb = K.T_CMB0 / a
-    comp = 4.0 * K.K_BOLTZ * K.SIGMA_T * K.A_RAD * T_cmb**4 / (K.M_E * K.C_LIGHT) * (T - T_cmb) * n_e
-    return rec + ce + ff + comp
-
-
 # ------------------------------------------------------------------------ helium
 # Readings for hydrogen + helium gas (Sec. "Physical Model", Eq. electron_density; the paper
 # cites Cen (1992), Hui & Gnedin (1997) and Abel et al. (1997) for the rates):
@@ -61,8 +53,7 @@ def cooling_rate(T, n_e, n_HI, n_HII, a):
 #   dielectronic recombination of HeII (Aldrovandi & Pequignot form used by Cen 1992), their
 #   recombination cooling, collisional excitation of HeII (Cen 1992), bremsstrahlung with
 #   Z^2 = 4 for HeIII.  Collisional ionisation and HeI collisional excitation are left out,
-#   like hydrogen's collisional ionisation.  Parity unpinned (implementation against
-#   implementation only).
+#   like hydrogen's collisional ionisation.
 T_HEI = 285335.0    # K, HeI ionisation temperature of the Hui & Gnedin fits
 T_HEII = 631515.0   # K, HeII
 
@@ -86,22 +77,51 @@ def alpha_di(T):
     return 1.90e-3 * T**-1.5 * np.exp(-470000.0 / T) * (1.0 + 0.3 * np.exp(-94000.0 / T))
 
 
+def cooling_coefficients(T, a):
+    """Cooling rate coefficients by process, each per product of the proper densities named
+    [erg cm^3 s^-1] (Compton per n_e [erg s^-1]):
+
+    rec_HII   case-B recombination cooling, per n_e n_HII (Hui & Gnedin 1997)
+    ce_HI     collisional excitation of HI, per n_e n_HI (Cen 1992)
+    ff        bremsstrahlung of a Z = 1 ion, per n_e n_i (Z^2 n_i for charge Z; Gaunt factor
+              of Cen 1992)
+    comp      Compton scattering off the CMB at T_cmb = T_cmb0 / a, per n_e
+    rec_HeII  HeII -> HeI recombination cooling, kT alpha_HeII, per n_e n_HeII
+    rec_HeIII HeIII -> HeII case-B recombination cooling, per n_e n_HeIII: the hydrogen fit
+              under the hydrogenic scaling Lambda_Z(T) = Z^3 Lambda_H(T / Z^2), Z = 2, i.e.
+              Z times hydrogen's coefficient at the same lambda = 2 T_ion / T (as for alpha)
+    di_HeII   dielectronic recombination cooling (the HeII 2p -> 1s energy per
+              recombination), per n_e n_HeII
+    ce_HeII   collisional excitation of HeII, per n_e n_HeII (Cen 1992)
+    """
+    T = _cmax(T, T_FLOOR)
+    lam = 2.0 * T_HI / T
+    lam3 = 2.0 * T_HEII / T
+    T_cmb = K.T_CMB0 / a
+    return dict(
+        rec_HII=3.435e-30 * T * lam**1.970 / (1.0 + (lam / 2.250) ** 0.376) ** 3.720,
+        ce_HI=7.5e-19 * np.exp(-118348.0 / T) / (1.0 + np.sqrt(T / 1e5)),
+        ff=1.42e-27 * (1.1 + 0.34 * np.exp(-((5.5 - np.log10(T)) ** 2) / 3.0)) * np.sqrt(T),
+        comp=4.0 * K.K_BOLTZ * K.SIGMA_T * K.A_RAD * T_cmb**4 / (K.M_E * K.C_LIGHT) * (T - T_cmb),
+        rec_HeII=K.K_BOLTZ * T * alpha_HeII_B(T),
+        rec_HeIII=2.0 * 3.435e-30 * T * lam3**1.970 / (1.0 + (lam3 / 2.250) ** 0.376) ** 3.720,
+        di_HeII=6.526e-11 * alpha_di(T),
+        ce_HeII=5.54e-17 * T**-0.397 * np.exp(-473638.0 / T) / (1.0 + np.sqrt(T / 1e5)),
+    )
+
+
+def cooling_rate(T, n_e, n_HI, n_HII, a):
+    """Total cooling Lambda per unit proper volume [erg cm^-3 s^-1] (proper densities)."""
+    c = cooling_coefficients(T, a)
+    return (c["rec_HII"] + c["ff"]) * n_e * n_HII + c["ce_HI"] * n_e * n_HI + c["comp"] * n_e
+
+
 def cooling_rate_he(T, n_e, n_HI, n_HII, n_HeII, n_HeIII, a):
     """Total cooling of hydrogen + helium gas per unit proper volume [erg cm^-3 s^-1]:
     the hydrogen terms of ``cooling_rate`` (with bremsstrahlung of all ions) plus HeII and
     HeIII recombination cooling, dielectronic recombination cooling and collisional
     excitation of HeII."""
-    T = _cmax(T, T_FLOOR)
-    lam = 2.0 * T_HI / T
-    rec = 3.435e-30 * T * lam**1.970 / (1.0 + (lam / 2.250) ** 0.376) ** 3.720 * n_e * n_HII
-    ce = 7.5e-19 * np.exp(-118348.0 / T) / (1.0 + np.sqrt(T / 1e5)) * n_e * n_HI
-    gff = 1.1 + 0.34 * np.exp(-((5.5 - np.log10(T)) ** 2) / 3.0)
-    ff = 1.42e-27 * gff * np.sqrt(T) * n_e * (n_HII + n_HeII + 4.0 * n_HeIII)
-    T_cmb = K.T_CMB0 / a
-    comp = 4.0 * K.K_BOLTZ * K.SIGMA_T * K.A_RAD * T_cmb**4 / (K.M_E * K.C_LIGHT) * (T - T_cmb) * n_e
-    rec_he2 = K.K_BOLTZ * T * alpha_HeII_B(T) * n_e * n_HeII
-    lam3 = 2.0 * T_HEII / T
-    rec_he3 = 8.0 * 3.435e-30 * T * lam3**1.970 / (1.0 + (lam3 / 2.250) ** 0.376) ** 3.720 * n_e * n_HeIII
-    di = 6.526e-11 * alpha_di(T) * n_e * n_HeII
-    ce_he2 = 5.54e-17 * T**-0.397 * np.exp(-473638.0 / T) / (1.0 + np.sqrt(T / 1e5)) * n_e * n_HeII
-    return rec + ce + ff + comp + rec_he2 + rec_he3 + di + ce_he2
+    c = cooling_coefficients(T, a)
+    return (c["rec_HII"] * n_e * n_HII + c["ce_HI"] * n_e * n_HI
+            + c["ff"] * n_e * (n_HII + n_HeII + 4.0 * n_HeIII) + c["comp"] * n_e
+            + (c["rec_HeII"] + c["di_HeII"] + c["ce_HeII"]) * n_e * n_HeII + c["rec_HeIII"] * n_e * n_HeIII)

@@ -7,7 +7,8 @@
 //  * rates: hydrogen as in physics.cuh; helium case-B recombination HeII -> HeI
 //    1.26e-14 (2 T_HeI/T)^0.75 plus dielectronic 1.9e-3 T^-1.5 e^{-470000/T} (1 + 0.3
 //    e^{-94000/T}), HeIII -> HeII the hydrogenic fit at 2 T_HeII/T (Hui & Gnedin 1997; Cen
-//    1992), all times the clumping factor; cooling adds HeII and HeIII recombination, dielectronic
+//    1992), all times the clumping factor; cooling adds HeII and HeIII recombination (HeIII by the
+//    hydrogenic scaling of hydrogen's, Lambda_Z(T) = Z^3 Lambda_H(T / Z^2)), dielectronic
 //    and HeII collisional-excitation cooling and bremsstrahlung of every ion (Z^2 = 4 for HeIII).
 //    As for hydrogen the fits are evaluated with one d/dT lane and chained to all partials.
 //  * S_HI: exact solution over dt of y' = A (n_H - y)(n_H + n_e,He - y) - G y with the helium
@@ -70,7 +71,9 @@ RT_HD HeRates<T> he_rates_direct(const PhysParams& P, const T& temp, bool cool) 
                     (1.0 + f.sqrtT * 3.1622776601683794e-3);
     r.c2 = 1.380649e-16 * f.temp * aHeII + 6.526e-11 * adi + ceHe2;
     const T q3 = fexp(0.376 * (loglam3 - 0.8109302162163288));
-    r.c3 = (8.0 * 3.435e-30) * f.temp * fexp(1.970 * loglam3 - 3.720 * flog(1.0 + q3));
+    // hydrogenic scaling Lambda_Z(T) = Z^3 Lambda_H(T / Z^2), Z = 2: Z times hydrogen's
+    // coefficient at the same lambda, as for the recombination coefficient a3
+    r.c3 = (2.0 * 3.435e-30) * f.temp * fexp(1.970 * loglam3 - 3.720 * flog(1.0 + q3));
     return r;
 }
 
