@@ -247,8 +247,11 @@ void harvest(rt_grid* g) {
     g->ev_used = 0;
 }
 
+enum HierarchyStatus { HIER_OK = 0, HIER_ODD, HIER_NOMEM };
+
+// lv[0] takes diag0 (freed with the grid) whatever the outcome
 template <class T>
-bool build_hierarchy(rt_grid* g, Hierarchy<T>& H, T* diag0, T* wx0, T* wy0, T* wz0) {
+HierarchyStatus build_hierarchy(rt_grid* g, Hierarchy<T>& H, T* diag0, T* wx0, T* wy0, T* wz0) {
     bool ok = true;
     Dims d = g->dims;
     Level<T> L;
@@ -261,7 +264,7 @@ bool build_hierarchy(rt_grid* g, Hierarchy<T>& H, T* diag0, T* wx0, T* wy0, T* w
     L.b = nullptr;
     H.lv.push_back(L);
     while (d.n() > TailMax<T>::value) {
-        if (d.nx % 2 || d.ny % 2 || d.nz % 2) return false;
+        if (d.nx % 2 || d.ny % 2 || d.nz % 2) return HIER_ODD;
         d.nx /= 2;
         d.ny /= 2;
         d.nz /= 2;
@@ -275,10 +278,10 @@ bool build_hierarchy(rt_grid* g, Hierarchy<T>& H, T* diag0, T* wx0, T* wy0, T* w
         c.x = dalloc<T>(n, ok);
         c.b = dalloc<T>(n, ok);
         for (void* p : {(void*)c.diag, (void*)c.wx, (void*)c.wy, (void*)c.wz, (void*)c.x, (void*)c.b}) H.owned.push_back(p);
-        if (!ok) return false;
+        if (!ok) return HIER_NOMEM;
         H.lv.push_back(c);
     }
-    return ok;
+    return HIER_OK;
 }
 
 template <class T>
@@ -637,7 +640,7 @@ void rt_destroy_grid(rt_grid* g) {
     cudaSetDevice(g->desc.device);
     double* bufs[] = {g->E0, g->n0, g->src, g->bE, g->wx, g->wy, g->wz, g->Ec, g->nc, g->ecc, g->Et, g->nt, g->ect,
                       g->step, g->diag, g->rhs, g->wE, g->x, g->r, g->z, g->p, g->q, g->partials, g->dots, g->scal,
-                      g->Xec, g->Xnc, g->Xet, g->Xnt};
+                      g->Xec, g->Xnc, g->Xet, g->Xnt, g->He10, g->He20, g->He1c, g->He2c, g->He1t, g->He2t};
     for (double* b : bufs) cudaFree(b);
     cudaFree(g->wxf);
     cudaFree(g->wyf);
@@ -778,20 +781,31 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out) {
         g->bf = dalloc<float>(n, ok);
         g->xf = dalloc<float>(n, ok);
         float* diag0 = dalloc<float>(n, ok);
-        if (ok && !build_hierarchy<float>(g, g->mgf, diag0, g->wxf, g->wyf, g->wzf)) {
-            set_detail("grid %dx%dx%d: a level above %d cells has an odd dimension", d.nx, d.ny, d.nz,
-                       TailMax<float>::value);
-            if (g->mgf.lv.empty()) cudaFree(diag0);
-            rt_destroy_grid(g);
-            return RT_EINVAL;
+        if (!ok) {
+            cudaFree(diag0);
+        } else {
+            const HierarchyStatus hs = build_hierarchy<float>(g, g->mgf, diag0, g->wxf, g->wyf, g->wzf);
+            if (hs == HIER_ODD) {
+                set_detail("grid %dx%dx%d: a level above %d cells has an odd dimension", d.nx, d.ny, d.nz,
+                           TailMax<float>::value);
+                rt_destroy_grid(g);
+                return RT_EINVAL;
+            }
+            if (hs == HIER_NOMEM) ok = false;
         }
     } else if (ok) {
         double* diag0 = dalloc<double>(n, ok);
-        if (ok && !build_hierarchy<double>(g, g->mgd, diag0, g->wx, g->wy, g->wz)) {
-            set_detail("grid %dx%dx%d: a level above %d cells has an odd dimension", d.nx, d.ny, d.nz,
-                       TailMax<double>::value);
-            rt_destroy_grid(g);
-            return RT_EINVAL;
+        if (!ok) {
+            cudaFree(diag0);
+        } else {
+            const HierarchyStatus hs = build_hierarchy<double>(g, g->mgd, diag0, g->wx, g->wy, g->wz);
+            if (hs == HIER_ODD) {
+                set_detail("grid %dx%dx%d: a level above %d cells has an odd dimension", d.nx, d.ny, d.nz,
+                           TailMax<double>::value);
+                rt_destroy_grid(g);
+                return RT_EINVAL;
+            }
+            if (hs == HIER_NOMEM) ok = false;
         }
     }
     if (!ok) {

@@ -114,3 +114,24 @@ def test_field_64_mixed_is_a_root_and_keeps_helium_in_bounds():
     assert H.rms(H.weights(st, U), f) <= 1e-8, stats
     assert np.all(nHeI >= 0) and np.all(nHeII >= 0) and np.all(nHeI + nHeII <= st.n_He * (1 + 1e-12))
     assert np.min(nHeI / st.n_He) < 0.5                  # the sources ionise helium
+
+
+def test_grid_destroy_returns_device_memory():
+    """rt_destroy_grid releases the whole workspace, the helium species buffers included
+    (100 MB of them per grid at 128^3): hydrogen and hydrogen + helium grids created and
+    destroyed three times leave the free device memory where it was."""
+    import ctypes
+    from paper_0908_2654_gb300 import _rt
+    L = _rt.lib()
+    for w in (W.stromgren_static(n=128), W.with_helium(W.stromgren_static(n=128))):
+        s = _solver(w, "mixed")
+        d = s.desc
+        s.close()
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(3):
+            h = ctypes.c_void_p()
+            _rt.check(L.rt_init_grid(ctypes.byref(d), ctypes.byref(h)), "rt_init_grid")
+            L.rt_destroy_grid(h)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] >= free0 - (16 << 20), w.get("helium", False)
