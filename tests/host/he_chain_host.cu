@@ -1,6 +1,8 @@
-// Host build of the GPU path's helium chain and hydrogen-with-helium-electrons Riccati solution
-// (helium.cuh, compiled for the CPU) so that tests can compare them with the oracle across
-// parameter regimes; derivatives through the same dual numbers the kernels use.
+// Host builds of the GPU path's cell physics (helium.cuh and physics.cuh, compiled for the
+// CPU) so that tests can compare them with the oracle across parameter regimes: the helium
+// chain, the Riccati solutions with and without helium electrons, the rate fits of both
+// chemistry paths and the face limiter; derivatives through the same dual numbers the kernels
+// use.
 #include <cstring>
 
 #include "../../paper_0908_2654_gb300/csrc/helium.cuh"
@@ -57,6 +59,48 @@ extern "C" {
 void riccati_n_host(int n, const double* y0, const double* nH, const double* A, const double* G, const double* dt,
                     double* y) {
     for (int i = 0; i < n; ++i) y[i] = riccati_n<double>(y0[i], nH[i], A[i], G[i], dt[i]);
+}
+
+}
+
+extern "C" {
+
+// hydrogen-only rate fits of the GPU path (physics.cuh t_rates: one d/dT lane, chained into a
+// two-lane dual with T as lane 0); outputs [4][n]: alpha (Hui & Gnedin), rf, ce, comp, with
+// d/dT of each in dout and the untouched second lane in dzero
+void t_rates_host(int n, const double* T, double a, double* out, double* dout, double* dzero) {
+    PhysParams P;
+    memset(&P, 0, sizeof(P));
+    P.recomb = 1;
+    P.a = a;
+    for (int i = 0; i < n; ++i) {
+        const TRates<Dual<2>> r = t_rates<2>(P, dvar<2>(T[i], 0), true, true);
+        const Dual<2>* v[4] = {&r.alpha, &r.rf, &r.ce, &r.comp};
+        for (int k = 0; k < 4; ++k) {
+            out[k * n + i] = v[k]->v;
+            dout[k * n + i] = v[k]->d[0];
+            dzero[k * n + i] = v[k]->d[1];
+        }
+    }
+}
+
+// Eq. limiter on n faces (Ei, Ej, ki, kj) as the face kernels evaluate it, and its derivative
+// in Ei through the dual-number form the adjoint uses
+void limiter_host(int n, const double* Ei, const double* Ej, const double* ki, const double* kj, double adx,
+                  double c, double E_min, double* D, double* D_t, double* dD_dEi) {
+    PhysParams P;
+    memset(&P, 0, sizeof(P));
+    P.adx = adx;
+    P.c = c;
+    P.E_min = E_min;
+    P.limiter = 0;
+    for (int i = 0; i < n; ++i) {
+        D[i] = limiter_face(P, Ei[i], Ej[i], ki[i], kj[i]);
+        const Dual<1> d = limiter_face_t<Dual<1>>(P, dvar<1>(Ei[i], 0), dconst<1>(Ej[i]), dconst<1>(ki[i]),
+                                                   dconst<1>(kj[i]));
+        D_t[i] = d.v;
+        dD_dEi[i] = d.d[0];
+    }
 }
 
 }

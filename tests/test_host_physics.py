@@ -152,3 +152,83 @@ def test_hydrogen_riccati_matches_oracle(host_lib):
     host_lib.riccati_n_host(ctypes.c_int(n), *[_p(a) for a in args], _p(y))
     ref = np.real(M.riccati_Sn(y0, nH, A, G, dt))
     assert np.max(np.abs(y - ref)) < 1e-13
+
+
+def test_hydrogen_rate_fits_match_oracle_over_temperature(host_lib):
+    """The hydrogen-only kernels' rates (physics.cuh t_rates: the Hui & Gnedin alpha and the
+    cooling coefficients rf = recombination + bremsstrahlung, ce, comp, each with d/dT from one
+    dual lane chained into the cell's partials) against the oracle's per-process coefficients
+    from 1 K to 1e9 K; the chained lane that is not T stays exactly zero."""
+    from oracle import rates as R
+    n = 400
+    T = np.logspace(0, 9, n)
+    a = 0.2
+    out, dout, dz = np.empty(4 * n), np.empty(4 * n), np.empty(4 * n)
+    host_lib.t_rates_host(ctypes.c_int(n), _p(_arr(T)), ctypes.c_double(a), _p(out), _p(dout), _p(dz))
+    out, dout = out.reshape(4, n), dout.reshape(4, n)
+    c = R.cooling_coefficients(T, a)
+    refs = (lambda t: R.alpha_B(t, "hg97"), lambda t: (lambda q: q["rec_HII"] + q["ff"])(R.cooling_coefficients(t, a)),
+            lambda t: R.cooling_coefficients(t, a)["ce_HI"], lambda t: R.cooling_coefficients(t, a)["comp"])
+    np.testing.assert_allclose(out[0], R.alpha_B(T, "hg97"), rtol=1e-13)
+    np.testing.assert_allclose(out[1], c["rec_HII"] + c["ff"], rtol=1e-13)
+    np.testing.assert_allclose(out[2], c["ce_HI"], rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(out[3], c["comp"], rtol=1e-13)
+    h = 1e-20
+    for k, f in enumerate(refs):
+        ref = np.imag(f(T + 1j * h * T)) / (h * T)
+        np.testing.assert_allclose(dout[k], ref, rtol=1e-10, atol=1e-300)
+    assert np.all(dz == 0.0)
+
+
+def test_face_limiter_matches_oracle(host_lib):
+    """Eq. limiter as the face kernels evaluate it (value form and dual form), against the
+    oracle's face_D on two-cell rows. The cases cover energy ratios over 60 decades, both
+    energies below E_min, optically thin faces (kappa = 0), equal energies (R = 0) and the
+    case kappa = R = 0. The dual form's dD/dE_i is compared with a complex step through the
+    oracle."""
+    from types import SimpleNamespace
+    from oracle import model as M
+    rng = np.random.default_rng(17)
+    n = 3000
+    adx, E_min = 3.1e21, 1e-35
+    Ei = 10 ** rng.uniform(-40, 20, n)
+    Ej = Ei * 10 ** rng.uniform(-30, 30, n)
+    ki = 10 ** rng.uniform(-30, -15, n)
+    kj = ki * 10 ** rng.uniform(-5, 5, n)
+    k = n // 10
+    ki[:k] = kj[:k] = 0.0                            # optically thin
+    Ej[k:2 * k] = Ei[k:2 * k]                        # no gradient
+    Ej[2 * k:3 * k] = Ei[2 * k:3 * k]
+    ki[2 * k:3 * k] = kj[2 * k:3 * k] = 0.0          # kappa = R = 0
+    Ei[3 * k:4 * k] *= 1e-30                         # both far below E_min
+    Ej[3 * k:4 * k] = Ei[3 * k:4 * k] * 3.0
+    D, Dt, dD = np.empty(n), np.empty(n), np.empty(n)
+    host_lib.limiter_host(ctypes.c_int(n), *[_p(_arr(v)) for v in (Ei, Ej, ki, kj)], ctypes.c_double(adx),
+                          ctypes.c_double(M.K.C_LIGHT), ctypes.c_double(E_min), _p(D), _p(Dt), _p(dD))
+    st = SimpleNamespace(limiter="new", a=1.0, dx=adx, E_min=E_min, shape=(1, n, 2),
+                         periodic=(False, False, False), D_const=0.0)
+
+    def oracle_D(ei):
+        E = np.stack([ei, Ej + 0 * ei], axis=-1)[None]
+        kap = np.stack([ki, kj], axis=-1)[None]
+        return M.face_D(st, E, kap, 0)[0, :, 0]
+
+    ref = np.real(oracle_D(Ei))
+    np.testing.assert_allclose(D, ref, rtol=1e-13)
+    np.testing.assert_allclose(Dt, D, rtol=1e-15)         # the dual quotient rounds differently (1 ulp)
+    h = 1e-20
+    cs = np.imag(oracle_D(Ei + 1j * h * Ei)) / (h * Ei)
+    # rounding scale of the chain rule dD/dR dR/dE_i, from the magnitudes of the quotient
+    # rules' terms: those of dR/dE_i, (E_f + |dE|/2) / (adx E_f^2), cancel when E_j << E_i
+    # (R saturates at 2 / adx); those of dD/dR, c / den and D (3 kappa_T + 2 R) / den with
+    # den = 6 kappa_T^2 + 3 kappa_T R + R^2, cancel as R -> 0 (dD/dR vanishes at R = 0)
+    Ef = np.real(M.spos(0.5 * (Ei + Ej), E_min))
+    R = np.abs(Ej - Ei) / (adx * Ef)
+    kT = 0.5 * (ki + kj)
+    den = 6.0 * kT**2 + 3.0 * kT * R + R**2
+    with np.errstate(divide="ignore", invalid="ignore"):
+        D_R_terms = (M.K.C_LIGHT + ref * (3.0 * kT + 2.0 * R)) / den
+    scale = D_R_terms * (Ef + 0.5 * np.abs(Ej - Ei)) / (adx * Ef**2)
+    has_derivative = ~((kT == 0) & (R == 0))         # kappa = R = 0: D jumps from c / R to c adx
+    err = np.abs(dD - cs)[has_derivative]
+    assert np.all(err <= 1e-9 * np.abs(cs[has_derivative]) + 1e-13 * scale[has_derivative])
