@@ -28,7 +28,8 @@ def row(vals, per=4):
     return "\n".join(out)
 
 
-def main():
+def render():
+    """The text of fastmath_tables.cuh."""
     ln2 = mp.log(2)
     exp_t = [float(mp.power(2, mp.mpf(j) / 64)) for j in range(64)]
     log_hi, log_lo, log_inv = [], [], []
@@ -68,8 +69,12 @@ constexpr double kLn2By64Lo = {ln2_64_lo!r};
 constexpr double kLn2Hi = {ln2_hi!r};
 constexpr double kLn2Lo = {ln2_lo!r};
 """
+    return src
+
+
+def main():
     with open(os.path.join(HERE, "fastmath_tables.cuh"), "w") as f:
-        f.write(src)
+        f.write(render())
 
 
 if __name__ == "__main__":
