@@ -44,10 +44,29 @@ def parse():
     return p.parse_args()
 
 
+L2_BYTES = 129e6   # GB300 L2
+
+
+def workload_sources(n):
+    """Source count of the n^3 field: 2000, scaled down with the volume below 128^3."""
+    return 2000 if n >= 128 else max(2, 2000 * n**3 // 256**3)
+
+
 def workload(n):
     import workloads as W
-    return W.reionization_field(n=n, nsrc=2000 if n >= 128 else max(2, 2000 * n**3 // 256**3),
-                                box_mpc=14.4 * n / 256, ndot_total=1e52 * (n / 256) ** 3)
+    return W.reionization_field(n=n, nsrc=workload_sources(n), box_mpc=14.4 * n / 256,
+                                ndot_total=1e52 * (n / 256) ** 3)
+
+
+def l2_note(n):
+    """How the timed steps stand to the L2 (the timing rule: inputs larger than L2, or a flush):
+    the working set is taken as the DRAM traffic of one Newton evaluation."""
+    ws = ASSEMBLE_DRAM_BYTES_PER_CELL * n**3
+    field = 8.0 * n**3 / 1e6
+    if ws > L2_BYTES:
+        return (f"inputs larger than L2 (one Newton evaluation moves {ws / 1e6:.0f} MB, each FP64 field "
+                f"{field:.1f} MB; L2 {L2_BYTES / 1e6:.0f} MB)")
+    return f"inputs smaller than L2 at this size (one Newton evaluation moves {ws / 1e6:.0f} MB); L2 not flushed"
 
 
 # FP64 flops per cell of one newton_assemble launch on this workload (mean over the five
@@ -426,14 +445,15 @@ def bench_line(args, res, world, peaks):
                    "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None,
                    "share": v["ms"] / res["ms"]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
     launches = sum(x["kernel_launches"] for x in res["stats"]) + len(res["stats"])
-    w_desc = f"reionization-like field {args.size}^3, 2000 sources, z=9, dt=1 Myr, theta=1"
+    w_desc = (f"reionization-like field {args.size}^3, {workload_sources(args.size)} sources, z=9, dt=1 Myr, "
+              "theta=1")
     line = {
         "metric": METRIC, "value": res["value"], "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": w_desc, "grid": args.size, "precision": "mixed (FP32 multigrid in FP64 Newton/CG)",
                    "newton_tol": args.newton_tol, "lin_rtol": args.lin_rtol, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (each FP64 field 134 MB at 256^3)"},
+                   "l2": l2_note(args.size)},
         "newton_iters": [x["newton_iters"] for x in res["stats"]],
         "linear_iters": [x["linear_iters"] for x in res["stats"]],
         "fp64": res["fp64"],

@@ -41,3 +41,14 @@ def test_bench_line_contract_and_rooflines():
     assert line["gpu_launches"] == 4 * 2970 + 4
     assert line["ms_per_step"] == pytest.approx(1190.0 / 4)
     json.loads(json.dumps(line))
+
+
+def test_config_describes_the_workload_at_each_size():
+    """The workload and L2 notes follow the grid: 2000 sources and fields above L2 at 256^3
+    (no flush needed); fewer sources and an honest 'not flushed' below."""
+    for n, nsrc, above in ((256, 2000, True), (128, 2000, True), (64, 31, False)):
+        args = argparse.Namespace(size=n, steps=4, warmup=3, newton_tol=1e-6, lin_rtol=1e-3)
+        cfg = bench.bench_line(args, _res(), 1, {"hbm_gbs": 6797.2})["config"]
+        assert f"{n}^3, {nsrc} sources" in cfg["workload"]
+        assert cfg["l2"].startswith("inputs larger than L2" if above else "inputs smaller than L2")
+        assert bench.workload_sources(n) == nsrc
