@@ -10,7 +10,9 @@
  * radiation_residual to zero with a globalised inexact Newton method.  Each
  * Newton system is reduced by a Schur complement to a modified radiation
  * equation (a 7-point symmetric operator in E), solved by conjugate gradients
- * preconditioned with geometric multigrid.  Hydrogen-only gas (N_s = 1).
+ * preconditioned with geometric multigrid.  Hydrogen-only gas (N_s = 1), or hydrogen +
+ * helium (N_s = 3: n_HI, n_HeI, n_HeII; rt_grid_desc.helium) with Eq. electron_density's
+ * helium case.
  *
  * Units.  All fields are in the paper's normalised comoving variables
  * (Eqs. units, scalings, proper_vars): x~ = x/u_x, t~ = t/u_t, rho~ = rho/u_d,
@@ -121,9 +123,10 @@ typedef struct {
     int line_search_cuts; /* step halvings                                                   */
     double norm0;         /* RMS norm of f at the initial iterate                            */
     double norm;          /* RMS norm of f at the returned state                             */
-    double change_norm;   /* RMS over the 3N unknowns of the step's change, scaled like the
-                             norm (E by max(|E^{n+1}|, |E^n|, E_floor), n_HI by n_H, e_c by
-                             the hydro internal energy): the measure a time-step controller
+    double change_norm;   /* RMS over the 3N (helium: 5N) unknowns of the step's change,
+                             scaled like the norm (E by max(|E^{n+1}|, |E^n|, E_floor), n_HI
+                             by n_H, helium by n_He, e_c by the hydro internal energy): the
+                             measure a time-step controller
                              compares with its tolerance (0 unless the step succeeded)      */
     int kernel_launches;  /* kernels this call launched                                      */
     int nhist;            /* entries used in the histories below                             */
@@ -137,12 +140,13 @@ typedef struct {
 typedef struct rt_grid rt_grid;   /* opaque */
 
 /* Allocate workspace and precompute the grey spectral constants (Eq. grey_definition) and
- * unit factors.  *out receives the handle.  Errors: RT_EINVAL (shape, units, parameters),
- * RT_ENOMEM, RT_ECUDA. */
+ * unit factors.  *out receives the handle (NULL on error).  All descriptor checks run before
+ * any CUDA call.  Errors: RT_EINVAL (shape, units, parameters), RT_ENOMEM, RT_ECUDA. */
 int rt_init_grid(const rt_grid_desc* desc, rt_grid** out);
 
-/* One implicit step (v): on entry *inout holds the advected state (E*, n_HI*; e_c is
- * ignored and taken as 0), on success it holds U^{n+1} with f(U^{n+1}) below newton_tol.
+/* One implicit step (v): on entry *inout holds the advected state (E*, n_HI*, and n_HeI*,
+ * n_HeII* on helium grids; e_c is ignored and taken as 0), on success it holds U^{n+1} with
+ * f(U^{n+1}) below newton_tol.
  * stats may be NULL.  Errors: RT_EINVAL, RT_ENOCONV, RT_ELINESEARCH, RT_ENONFINITE,
  * RT_ELINEAR, RT_ECUDA; *inout is unchanged on error. */
 int rt_implicit_step(rt_grid* g, const rt_step_inputs* in, rt_state* inout, rt_step_stats* stats);
@@ -154,7 +158,9 @@ int rt_residual(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const
                 double* f_e, double* f_n, double* f_E);
 
 /* Schur complement of the Newton system at U (Sec. "Algorithm": the reduction to a modified
- * radiation equation): S = J_EE - J_Eu J_uu^-1 J_uE as diag (per cell) and the three +x/+y/+z
+ * radiation equation; u = the cell-local unknowns, (e_c, n_HI) or on helium grids (e_c, n_HI,
+ * n_HeI, n_HeII), which U and U_n must then carry):
+ * S = J_EE - J_Eu J_uu^-1 J_uE as diag (per cell) and the three +x/+y/+z
  * face couplings w (S_ij = -w on the face between i and its + neighbour; S is symmetric), and
  * rhs = -f_E + J_Eu J_uu^-1 f_u.  The operator is also kept as the one rt_schur_solve uses.
  * Errors: RT_EINVAL, RT_ECUDA. */
@@ -256,8 +262,12 @@ int rt_advect(rt_grid* g, const rt_step_inputs* in, const rt_state* src, rt_stat
  * Same argument rules and errors as rt_advect. */
 int rt_advect_adjoint(rt_grid* g, const rt_step_inputs* in, const rt_state* lam_star, rt_state* lam);
 
+/* Free the grid's whole workspace; g is invalid afterwards.  NULL is a no-op. */
 void rt_destroy_grid(rt_grid* g);
+/* Static message for an error code ("unknown error" for codes outside the list). */
 const char* rt_error_string(int code);
+/* Detail text of the last error this library recorded on the calling host thread (a
+ * per-thread buffer, overwritten by that thread's next error; empty if none). */
 const char* rt_last_error_detail(void);
 
 /* Grey constants the library derived at init, in CGS: sigma_E [cm^2], sigma_G [cm^2/erg],

@@ -828,7 +828,10 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out) {
 }
 
 int rt_grey_constants(const rt_grid* g, double* sigma_E, double* sigma_G, double* eps_src) {
-    if (!g) return RT_EINVAL;
+    if (!g) {
+        set_detail("null grid");
+        return RT_EINVAL;
+    }
     if (sigma_E) *sigma_E = g->grey.sigma_E;
     if (sigma_G) *sigma_G = g->grey.sigma_G;
     if (eps_src) *eps_src = g->grey.eps_src;
@@ -1052,8 +1055,10 @@ int rt_residual_helium(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n
 int rt_schur_system(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U, double* diag,
                     double* wx, double* wy, double* wz, double* rhs) {
     if (!g || !U_n || !U || !U_n->E || !U_n->n_HI || !U->E || !U->n_HI || !U->e_c ||
-        (g->desc.helium && (!U_n->n_HeI || !U_n->n_HeII || !U->n_HeI || !U->n_HeII)))
+        (g->desc.helium && (!U_n->n_HeI || !U_n->n_HeII || !U->n_HeI || !U->n_HeII))) {
+        set_detail("null grid or state array");
         return RT_EINVAL;
+    }
     int rc = validate_inputs(g, in);
     if (rc) return rc;
     RT_CUDA(cudaSetDevice(g->desc.device));
@@ -1091,7 +1096,10 @@ int rt_schur_system(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, c
 }
 
 int rt_schur_solve(rt_grid* g, const double* b, double* x, double rtol, int max_iters, int* iters) {
-    if (!g || !b || !x || !(rtol > 0) || max_iters < 1) return RT_EINVAL;
+    if (!g || !b || !x || !(rtol > 0) || max_iters < 1) {
+        set_detail("rt_schur_solve needs a grid, b, x, rtol > 0 and max_iters >= 1");
+        return RT_EINVAL;
+    }
     if (!g->schur_ready) {
         set_detail("rt_schur_solve needs a preceding rt_schur_system");
         return RT_EINVAL;
@@ -1119,7 +1127,10 @@ int rt_eval_elementary(int fn, const double* x, double* y, long long n, void* st
 }
 
 int rt_set_profiling(rt_grid* g, int on) {
-    if (!g) return RT_EINVAL;
+    if (!g) {
+        set_detail("null grid");
+        return RT_EINVAL;
+    }
     RT_CUDA(cudaSetDevice(g->desc.device));
     RT_CUDA(cudaStreamSynchronize(g->stream));
     g->prof_on = on != 0;
@@ -1133,7 +1144,10 @@ int rt_set_profiling(rt_grid* g, int on) {
 }
 
 int rt_get_profile(rt_grid* g, rt_kernel_profile* out, int max_entries, int* n_entries) {
-    if (!g || (!out && max_entries > 0)) return RT_EINVAL;
+    if (!g || (!out && max_entries > 0)) {
+        set_detail("null grid, or no output array for max_entries > 0");
+        return RT_EINVAL;
+    }
     RT_CUDA(cudaSetDevice(g->desc.device));
     RT_CUDA(cudaStreamSynchronize(g->stream));
     harvest(g);
@@ -1154,7 +1168,10 @@ int rt_get_profile(rt_grid* g, rt_kernel_profile* out, int max_entries, int* n_e
 }
 
 int rt_fold_energy(rt_grid* g, double* e_h, const double* e_c) {
-    if (!g || !e_h || !e_c) return RT_EINVAL;
+    if (!g || !e_h || !e_c) {
+        set_detail("null grid or energy array");
+        return RT_EINVAL;
+    }
     RT_CUDA(cudaSetDevice(g->desc.device));
     run(g, K_ADD, (double)g->n * 24, [&] { launch_add(g->n, e_c, e_h, g->stream); });
     if (g->prof_on) {

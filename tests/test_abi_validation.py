@@ -84,26 +84,34 @@ def test_init_grid_rejects_null_arguments(L):
 
 
 def test_null_grid_handle_is_rejected_by_every_entry_point(L):
+    """Every entry point rejects a NULL grid with RT_EINVAL and records its own detail text
+    (checked against a different error's text recorded just before)."""
     inp, st, st2 = _rt.StepInputs(), _rt.State(), _rt.State()
     stats = _rt.StepStats()
     r = ctypes.c_double()
     n = ctypes.c_int()
-    assert L.rt_implicit_step(None, ctypes.byref(inp), ctypes.byref(st), ctypes.byref(stats)) == _rt.RT_EINVAL
-    assert L.rt_residual(None, ctypes.byref(inp), ctypes.byref(st), ctypes.byref(st2), None, None, None) == _rt.RT_EINVAL
-    assert L.rt_residual_helium(None, ctypes.byref(inp), ctypes.byref(st), ctypes.byref(st2),
-                                None, None, None, None, None) == _rt.RT_EINVAL
-    assert L.rt_schur_system(None, ctypes.byref(inp), ctypes.byref(st), ctypes.byref(st2),
-                             None, None, None, None, None) == _rt.RT_EINVAL
-    assert L.rt_schur_solve(None, None, None, 1e-6, 10, ctypes.byref(n)) == _rt.RT_EINVAL
-    assert L.rt_adjoint_step(None, ctypes.byref(inp), ctypes.byref(st), ctypes.byref(st2), ctypes.byref(st),
-                             ctypes.byref(st2), None, None) == _rt.RT_EINVAL
-    assert L.rt_advect(None, ctypes.byref(inp), ctypes.byref(st), ctypes.byref(st2), None, None,
-                       ctypes.byref(r)) == _rt.RT_EINVAL
-    assert L.rt_advect_adjoint(None, ctypes.byref(inp), ctypes.byref(st), ctypes.byref(st2)) == _rt.RT_EINVAL
-    assert L.rt_fold_energy(None, None, None) == _rt.RT_EINVAL
-    assert L.rt_grey_constants(None, ctypes.byref(r), None, None) == _rt.RT_EINVAL
-    assert L.rt_set_profiling(None, 1) == _rt.RT_EINVAL
-    assert L.rt_get_profile(None, None, 0, ctypes.byref(n)) == _rt.RT_EINVAL
+    B = ctypes.byref
+    calls = {
+        "rt_implicit_step": lambda: L.rt_implicit_step(None, B(inp), B(st), B(stats)),
+        "rt_residual": lambda: L.rt_residual(None, B(inp), B(st), B(st2), None, None, None),
+        "rt_residual_helium": lambda: L.rt_residual_helium(None, B(inp), B(st), B(st2), None, None, None, None,
+                                                           None),
+        "rt_schur_system": lambda: L.rt_schur_system(None, B(inp), B(st), B(st2), None, None, None, None, None),
+        "rt_schur_solve": lambda: L.rt_schur_solve(None, None, None, 1e-6, 10, B(n)),
+        "rt_adjoint_step": lambda: L.rt_adjoint_step(None, B(inp), B(st), B(st2), B(st), B(st2), None, None),
+        "rt_advect": lambda: L.rt_advect(None, B(inp), B(st), B(st2), None, None, B(r)),
+        "rt_advect_adjoint": lambda: L.rt_advect_adjoint(None, B(inp), B(st), B(st2)),
+        "rt_fold_energy": lambda: L.rt_fold_energy(None, None, None),
+        "rt_grey_constants": lambda: L.rt_grey_constants(None, B(r), None, None),
+        "rt_set_profiling": lambda: L.rt_set_profiling(None, 1),
+        "rt_get_profile": lambda: L.rt_get_profile(None, None, 0, B(n)),
+    }
+    for name, call in calls.items():
+        assert L.rt_eval_elementary(9, None, None, 1, None) == _rt.RT_EINVAL
+        marker = L.rt_last_error_detail().decode()
+        assert call() == _rt.RT_EINVAL, name
+        detail = L.rt_last_error_detail().decode()
+        assert detail and detail != marker, name
     L.rt_destroy_grid(None)                # a no-op
 
 
