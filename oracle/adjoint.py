@@ -32,6 +32,7 @@ from . import newton as N
 
 
 def ionised_fraction(nHI, nH):
+    """Objective J of the gradient checks: the volume-averaged ionised fraction 1 - <n_HI/n_H>."""
     return float(1.0 - np.mean(nHI / nH))
 
 

@@ -26,21 +26,28 @@ from . import constants as K
 
 
 class FlatLCDM:
+    """Flat matter + Lambda expansion (the Friedmann equation of Sec. "Physical Model" with
+    Omega_m + Omega_L = 1); times in seconds since the big bang."""
+
     def __init__(self, Omega_m=0.3, Omega_L=0.7, h=0.7, **_):
         self.Om, self.OL, self.h = Omega_m, Omega_L, h
         self.H0 = h * K.H100
 
     def a(self, t):
+        """Scale factor: (Om/OL)^{1/3} sinh^{2/3}(1.5 sqrt(OL) H0 t)."""
         return (self.Om / self.OL) ** (1 / 3) * np.sinh(1.5 * math.sqrt(self.OL) * self.H0 * t) ** (2 / 3)
 
     def adot(self, t):
+        """da/dt = H0 a sqrt(Om / a^3 + OL)."""
         a = self.a(t)
         return self.H0 * a * np.sqrt(self.Om / a**3 + self.OL)
 
     def t_of_a(self, a):
+        """Inverse of a(t)."""
         return 2.0 / (3.0 * math.sqrt(self.OL) * self.H0) * np.arcsinh(math.sqrt(self.OL / self.Om) * a**1.5)
 
     def t_of_z(self, z):
+        """Time at redshift z (a = 1 / (1 + z))."""
         return self.t_of_a(1.0 / (1.0 + z))
 
 
@@ -52,10 +59,12 @@ class OpenNoLambda:
         self.Om = 2.0 * q0
 
     def adot(self, t):
+        """da/dt = H0 a sqrt(Om / a^3 + (1 - Om) / a^2) (curvature instead of Lambda)."""
         a = self.a(t)
         return self.H0 * a * math.sqrt(self.Om / a**3 + (1 - self.Om) / a**2)
 
     def a(self, t):
+        """Scale factor: (1.5 H0 t)^{2/3} for Om = 1, else the parametric cycloid in eta."""
         if abs(self.Om - 1.0) < 1e-12:
             return (1.5 * self.H0 * t) ** (2.0 / 3.0)
         Om = self.Om
@@ -64,9 +73,11 @@ class OpenNoLambda:
         return Om / (2 * (1 - Om)) * (math.cosh(eta) - 1)
 
     def t_of_z(self, z):
+        """Time at redshift z (a = 1 / (1 + z))."""
         return self.t_of_a(1.0 / (1.0 + z))
 
     def t_of_a(self, a):
+        """Inverse of a(t): the cycloid's eta from a, then t(eta)."""
         if abs(self.Om - 1.0) < 1e-12:
             return 2.0 / (3.0 * self.H0) * a**1.5
         Om = self.Om
@@ -92,13 +103,13 @@ def sg_ifront(abar, q0, z0, H0, ndot, alpha, nH0):
     """
     lam = alpha * nH0 / H0 / (1.0 + z0)
 
-    def bracket(a):
+    def bracket(a):       # the square-root argument of Eq. SG-F
         return 1.0 - 2.0 * q0 + 2.0 * q0 * (1.0 + z0) / a
 
-    def F(a):
+    def F(a):             # Eq. SG-F
         return (2.0 - 4.0 * q0 - 2.0 * q0 * (1.0 + z0) / a) * math.sqrt(bracket(a))
 
-    def tau(a):
+    def tau(a):           # Eq. SG-tau
         return lam / (6.0 * q0**2 * (1.0 + z0) ** 2) * (F(a) - F(1.0))
 
     val, _ = integrate.quad(lambda a: math.exp(tau(a)) / math.sqrt(bracket(a)), 1.0, abar,
@@ -109,7 +120,7 @@ def sg_ifront(abar, q0, z0, H0, ndot, alpha, nH0):
 
 def ifront_ode(t0, t1, a_of_t, ndot, alpha, n_comoving, V0=0.0, rtol=1e-11):
     """Integrate n_c dV_c/dt = Ndot - alpha n_c^2 V_c / a^3 from t0 to t1; returns V_c(t1) [cm^3]."""
-    def rhs(t, V):
+    def rhs(t, V):        # dV_c/dt
         return [ndot / n_comoving - alpha * n_comoving * V[0] / a_of_t(t) ** 3]
     sol = integrate.solve_ivp(rhs, (t0, t1), [V0], method="DOP853", rtol=rtol, atol=1e-30 * 0 + 1e-3)
     return float(sol.y[0, -1])

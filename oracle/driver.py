@@ -23,6 +23,8 @@ def energy_from_temperature(T, rho_b, nHI, v):
 
 
 def cosmology_of(w):
+    """The workload's expansion history (None for a static run): the Lambda-free models of
+    Table 1 when the workload names q0, flat LCDM otherwise."""
     c = w.get("cosmology")
     if c is None:
         return None
@@ -43,6 +45,7 @@ def time_grid(w):
 
 
 def expansion(w, t):
+    """(a, da/dt) at time t; (1, 0) for a static run."""
     cos = cosmology_of(w)
     if cos is None:
         return 1.0, 0.0
@@ -64,6 +67,8 @@ class Run:
         self.step_index = 0
 
     def make_step(self, a=None, adot=None, dt=None):
+        """The implicit step (v) from the current state: a and adot at the step's midpoint
+        time unless given."""
         w = self.w
         if a is None:
             a, adot = expansion(w, self.t + 0.5 * self.dt)
@@ -76,6 +81,8 @@ class Run:
             **self.grey)
 
     def advance(self, tol=1e-11, **kw):
+        """Solve one step (v) to the RMS norm tol and hand it over: E and n_HI replaced,
+        e_h += e_c, t += dt.  Returns the root U and the Newton record."""
         st = self.make_step()
         U, info = N.solve_step(st, tol=tol, **kw)
         e_c, nHI, E = U

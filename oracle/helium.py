@@ -58,10 +58,12 @@ class HeStep(M.Step):
 
     @property
     def n_H(self):
+        """Hydrogen number density (1 - Y) rho / m_H."""
         return (1.0 - self.Y) * self.rho_b / K.M_H
 
     @property
     def n_He(self):
+        """Helium number density Y rho / (4 m_H)."""
         return self.Y * self.rho_b / (K.M_HE_OVER_M_H * K.M_H)
 
 
@@ -71,6 +73,9 @@ def electrons(st, nHI, nHeI, nHeII):
 
 
 def temperature(st, e_c, nHI, nHeI, nHeII):
+    """T from the specific internal energy (Eqs. eos, temperature) with the particle count of
+    hydrogen + helium gas, n_tot = n_H + n_He + n_e (Eq. electron_density); T_iso when
+    isothermal."""
     if st.isothermal:
         return st.T_iso + 0.0 * nHI
     v2 = st.v[0] ** 2 + st.v[1] ** 2 + st.v[2] ** 2
@@ -181,6 +186,8 @@ def _scales(st, U):
 
 
 def jacobian(st, U, bE=None, freeze=False):
+    """Complex-step Jacobian of the 5N residual: the hydrogen oracle's routine with this
+    residual and the helium scales."""
     return N.jacobian(st, U, bE, freeze, residual=residual, scales=_scales)
 
 
@@ -207,7 +214,7 @@ def local_solve(st, U, tol=1e-14, maxit=60, h=1e-30):
     scl = _scales(st, U).reshape((NF,) + st.shape)
     w = weights(st, U)
 
-    def local_f(u):
+    def local_f(u):             # the local equations at u, with E fixed
         Ut = U.astype(complex) if np.iscomplexobj(u[0]) else U.copy()
         for j, i in enumerate(idx):
             Ut[i] = u[j]
@@ -216,7 +223,7 @@ def local_solve(st, U, tol=1e-14, maxit=60, h=1e-30):
         f = [] if iso else [Ut[0] - Se]
         return f + [Ut[1] - S[0], Ut[2] - S[1], Ut[3] - S[2]]
 
-    def scaled(f):
+    def scaled(f):              # max over the components of the weighted local residual
         return np.max(np.stack([np.abs(np.real(fi)) * w[i] for fi, i in zip(f, idx)]), axis=0)
 
     u = _clamp(st, [U[i] for i in idx], iso)
@@ -264,6 +271,8 @@ def local_solve(st, U, tol=1e-14, maxit=60, h=1e-30):
 
 
 def initial_iterate(st):
+    """Start of the Newton iteration: e_c = 0, the species at their start-of-step values and
+    E^n + dt 4 pi eta (the local solve that follows moves the species to S(E))."""
     return np.stack([np.zeros(st.shape), st.nHI_n.copy(), st.nHeI_n.copy(), st.nHeII_n.copy(),
                      st.E_n + st.dt * M.emissivity(st)])
 
@@ -333,12 +342,14 @@ class Run:
         self._h.e_h = energy_from_temperature(w["T0"], w["rho_b"], self._h.nHI, self.nHeI, self.nHeII, self.Y, w["v"])
 
     def make_step(self):
+        """The hydrogen run's step with the helium state and grey constants added."""
         from dataclasses import fields
         base = self._h.make_step()
         kw = {f.name: getattr(base, f.name) for f in fields(base)}
         return HeStep(**kw, Y=self.Y, nHeI_n=self.nHeI, nHeII_n=self.nHeII, **self.helium_grey)
 
     def advance(self, tol=1e-11):
+        """Solve one hydrogen + helium step and hand it over (all species, e_h += e_c)."""
         st = self.make_step()
         U, info = solve_step(st, tol=tol)
         e_c, nHI, nHeI, nHeII, E = U
@@ -350,4 +361,5 @@ class Run:
 
     @property
     def t(self):
+        """Current time."""
         return self._h.t

@@ -54,6 +54,7 @@ def cabs(x):
 
 
 def cmax(x, c):
+    """max(x, c) compared on real parts (complex-step safe)."""
     return np.where(np.real(x) >= np.real(c), x, c)
 
 
@@ -99,14 +100,17 @@ class Step:
 
     @property
     def shape(self):
+        """Array shape [z][y][x]."""
         return (self.nz, self.ny, self.nx)
 
     @property
     def N(self):
+        """Number of cells."""
         return self.nx * self.ny * self.nz
 
     @property
     def n_H(self):
+        """Hydrogen number density rho / m_H (X = 1)."""
         return self.rho_b / K.M_H
 
 
@@ -288,6 +292,8 @@ def local_residual(st, e_c, nHI, E):
 
 
 def internal_energy_h(st):
+    """Specific internal energy of the hydro state, e_h - |v|^2 / 2 (Eq. eos with e the total
+    specific energy)."""
     v2 = st.v[0] ** 2 + st.v[1] ** 2 + st.v[2] ** 2
     return st.e_h - 0.5 * v2
 

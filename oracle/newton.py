@@ -195,7 +195,7 @@ def local_solve(st, U, tol=1e-14, maxit=60):
     sn = st.n_H
     eint_h = M.internal_energy_h(st)
 
-    def scaled(fe, fn):
+    def scaled(fe, fn):         # max of the weighted local residual components
         return np.maximum(np.abs(fe) / se, np.abs(fn) / sn)
 
     nHI = np.clip(nHI, 1e-300, st.n_H)
