@@ -29,6 +29,8 @@ METRIC = "cell-steps/s of implicit FLD+chem solve, 256^3, mixed vs FP64; V-cycle
 
 
 def parse():
+    """Command line: the driver's --gpus/--steps/--warmup/--impl plus size, tolerances and
+    switches for the optional measurements."""
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=4)
@@ -53,6 +55,8 @@ def workload_sources(n):
 
 
 def workload(n):
+    """The bench's reionization field at n^3 (the 256^3 cell size; box and photon rate scale
+    with the volume)."""
     import workloads as W
     return W.reionization_field(n=n, nsrc=workload_sources(n), box_mpc=14.4 * n / 256,
                                 ndot_total=1e52 * (n / 256) ** 3)
@@ -84,6 +88,7 @@ FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.07
 
 
 def load_peaks():
+    """MEASURED_PEAKS.json at the repository root, or None."""
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
@@ -94,6 +99,9 @@ def load_peaks():
 
 
 class ClockSampler:
+    """nvidia-smi sampling of SM clocks, power and throttle reasons every 200 ms while the
+    timed region runs (a context manager); summary() gives the median clock and reasons."""
+
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
@@ -123,6 +131,7 @@ class ClockSampler:
             self.lines = [l for l in out.splitlines() if l.strip()]
 
     def summary(self):
+        """{sm_mhz: median under load, sm_max_mhz, reasons: active throttle reasons, samples}."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for l in self.lines:
@@ -189,6 +198,11 @@ def job_rate(world, cells, steps, ms_max):
 
 
 def run_gpu(args, rank, world, local_rank):
+    """The GPU arm on this rank: W warm-up and K timed mixed-precision steps of the field
+    (barrier and synchronise around the timed region; the library's per-kernel CUDA events
+    run on its stream inside that region, giving the kernel durations of the rooflines), then
+    the all-FP64 comparison, the end-to-end run from pinned host memory and the advection
+    pre-step.  Returns the results bench_line turns into the JSON line."""
     import torch
     import torch.distributed as dist
 
@@ -354,34 +368,40 @@ def densest_corner(w, m):
 
 
 def time_oracle_steps(w, m, nsteps, tol):
+    """Time nsteps oracle steps on the m^3 sub-block of w around its densest corner: returns
+    (cell-steps/s, wall seconds, sources inside, cores used).  Cores used = process CPU time
+    over wall time, which counts any threads numpy or SciPy start."""
     from oracle import driver
     sub = oracle_sample(w, m, densest_corner(w, m))
     r = driver.Run(sub)
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     for _ in range(nsteps):
         r.advance(tol=tol)
-    dt = time.perf_counter() - t0
-    return m**3 * nsteps / dt, dt, int(len(sub["src_index"]))
+    dt, cpu = time.perf_counter() - t0, time.process_time() - c0
+    return m**3 * nsteps / dt, dt, int(len(sub["src_index"])), max(1, int(round(cpu / dt)))
 
 
 def cpu_baseline(w, tol):
+    """The oracle timed on a bounded sample of the bench workload (one step of a 24^3 block)."""
     m = 24
-    value, secs, nsrc = time_oracle_steps(w, m, 1, tol)
-    return {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+    value, secs, nsrc, cores = time_oracle_steps(w, m, 1, tol)
+    return {"value": value, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
             "sample": f"one implicit step of a {m}^3 periodic sub-block of the {w['nx']}^3 field "
-                      f"({nsrc} sources inside), FP64 numpy/SciPy oracle, single thread, {secs:.1f} s"}
+                      f"({nsrc} sources inside), FP64 numpy/SciPy oracle, {secs:.1f} s"}
 
 
 def run_reference(args):
+    """The reference arm: the oracle, as it stands, on the host cores (16^3 sub-blocks of the
+    same field, K timed steps after W warm-up steps); prints its JSON line."""
     n = args.size
     w = workload(n)
     m = 16
     for _ in range(args.warmup):
         time_oracle_steps(w, m, 1, args.newton_tol)
-    value, secs, nsrc = time_oracle_steps(w, m, args.steps, args.newton_tol)
-    cpu = {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+    value, secs, nsrc, cores = time_oracle_steps(w, m, args.steps, args.newton_tol)
+    cpu = {"value": value, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
            "sample": f"{args.steps} implicit steps of a {m}^3 periodic sub-block of the {n}^3 field "
-                     f"({nsrc} sources), FP64 numpy/SciPy oracle, single thread"}
+                     f"({nsrc} sources), FP64 numpy/SciPy oracle"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -469,6 +489,7 @@ def bench_line(args, res, world, peaks):
 
 
 def main():
+    """Run the selected arm; under torchrun rank 0 prints the one JSON line."""
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -21,6 +21,8 @@ RT_LIMITER_LAGGED, RT_LIMITER_CONST = 0, 1
 
 
 class GridDesc(ctypes.Structure):
+    """rt_grid_desc: grid shape, units, physics switches and solver parameters."""
+
     _fields_ = [
         ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
         ("dx", ctypes.c_double),
@@ -41,6 +43,8 @@ class GridDesc(ctypes.Structure):
 
 
 class StepInputs(ctypes.Structure):
+    """rt_step_inputs: the hydro state, expansion and sources of one step (device pointers)."""
+
     _fields_ = [
         ("rho_b", ctypes.c_void_p), ("e_h", ctypes.c_void_p),
         ("vx", ctypes.c_void_p), ("vy", ctypes.c_void_p), ("vz", ctypes.c_void_p),
@@ -52,11 +56,15 @@ class StepInputs(ctypes.Structure):
 
 
 class State(ctypes.Structure):
+    """rt_state: E, n_HI, e_c (and n_HeI, n_HeII on helium grids), device pointers."""
+
     _fields_ = [("E", ctypes.c_void_p), ("n_HI", ctypes.c_void_p), ("e_c", ctypes.c_void_p),
                 ("n_HeI", ctypes.c_void_p), ("n_HeII", ctypes.c_void_p)]
 
 
 class StepStats(ctypes.Structure):
+    """rt_step_stats: Newton, line-search and CG counts, norms and their histories."""
+
     _fields_ = [
         ("newton_iters", ctypes.c_int), ("residual_evals", ctypes.c_int),
         ("linear_iters", ctypes.c_int), ("line_search_cuts", ctypes.c_int),
@@ -69,6 +77,7 @@ class StepStats(ctypes.Structure):
     ]
 
     def as_dict(self):
+        """The counters and the used part of each history as a plain dict."""
         d = {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("hist")}
         d["hist_norm"] = list(self.hist_norm[: self.nhist])
         d["hist_lam"] = list(self.hist_lam[: self.nhist])
@@ -77,6 +86,8 @@ class StepStats(ctypes.Structure):
 
 
 class KernelProfile(ctypes.Structure):
+    """rt_kernel_profile: launches, event time and algorithmic bytes of one kernel class."""
+
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int), ("ms", ctypes.c_double),
                 ("bytes", ctypes.c_double)]
 
@@ -130,6 +141,8 @@ def lib():
 
 
 class RTError(RuntimeError):
+    """A non-zero return code of the library, with its message and detail text."""
+
     def __init__(self, code, where):
         L = lib()
         self.code = code
@@ -139,6 +152,7 @@ class RTError(RuntimeError):
 
 
 def check(code, where):
+    """Raise RTError unless code is RT_OK."""
     if code != RT_OK:
         raise RTError(code, where)
 

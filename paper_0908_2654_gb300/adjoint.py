@@ -73,8 +73,13 @@ def adjoint_sweep(s, ckpts, lam_E, lam_n, lam_eh, nsrc):
 
 
 class IonizedFraction(torch.autograd.Function):
+    """J = volume-averaged ionised fraction after nsteps implicit steps, as a function of the
+    source rates and the clumping field; backward runs the discrete adjoint of every step
+    (rt_adjoint_step, and rt_advect_adjoint with advection) from the forward checkpoints."""
+
     @staticmethod
     def forward(ctx, ndot, clump, w, nsteps, options):
+        """Run the forward steps on the GPU, keeping the per-step checkpoints for backward."""
         s, ckpts, J = _run_forward(w, ndot, clump, nsteps, options or {})
         ctx.solver = s
         ctx.ckpts = ckpts
@@ -84,6 +89,7 @@ class IonizedFraction(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, gJ):
+        """dJ/dNdot and dJ/dC by the adjoint sweep; frees the forward solver."""
         s = ctx.solver
         lam_E = torch.zeros_like(s.E)
         lam_n = -1.0 / (s.rho.numel() * s.rho)       # dJ/dn_HI of the final state

@@ -20,6 +20,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxe
 
 
 def nvcc():
+    """Path of nvcc (PATH, else the CUDA default); raises if absent."""
     exe = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(exe):
         raise RuntimeError("nvcc not found")
@@ -36,6 +37,8 @@ def _compile(src, extra):
 
 
 def build(verbose=False, extra=()):
+    """Compile every source for sm_103a (in parallel) and link librtfld.so; returns its path.
+    extra: additional nvcc flags."""
     os.makedirs(OBJDIR, exist_ok=True)
     with concurrent.futures.ThreadPoolExecutor(len(SOURCES)) as ex:
         results = list(ex.map(lambda s: _compile(s, list(extra)), SOURCES))

@@ -13,18 +13,23 @@ H100 = 100.0 * 1e5 / 3.0856775814913673e24   # 100 km/s/Mpc in 1/s
 
 
 class FlatLCDM:
+    """Flat matter + Lambda expansion; times in seconds since the big bang."""
+
     def __init__(self, Omega_m=0.3, Omega_L=0.7, h=0.7, **_):
         self.Om, self.OL = Omega_m, Omega_L
         self.H0 = h * H100
 
     def a(self, t):
+        """Scale factor at time t."""
         return (self.Om / self.OL) ** (1.0 / 3.0) * math.sinh(1.5 * math.sqrt(self.OL) * self.H0 * t) ** (2.0 / 3.0)
 
     def adot(self, t):
+        """da/dt = H0 a sqrt(Om / a^3 + OL)."""
         a = self.a(t)
         return self.H0 * a * math.sqrt(self.Om / a**3 + self.OL)
 
     def t_of_z(self, z):
+        """Time at redshift z."""
         a = 1.0 / (1.0 + z)
         return 2.0 / (3.0 * math.sqrt(self.OL) * self.H0) * math.asinh(math.sqrt(self.OL / self.Om) * a**1.5)
 
@@ -38,6 +43,9 @@ def _sinh_minus_x(u):
 
 
 class LambdaFree:
+    """Lambda = 0 expansion with Omega_m = 2 q0 (0 < q0 <= 1/2); times in seconds since the
+    big bang."""
+
     def __init__(self, q0, h, **_):
         self.q0 = q0
         self.Om = 2.0 * q0
@@ -50,6 +58,7 @@ class LambdaFree:
             self.B = self.Om / (2.0 * (1.0 - self.Om) ** 1.5)
 
     def a(self, t):
+        """Scale factor at time t (the cycloid's u by Newton's method when open)."""
         if self.eds:
             return (1.5 * self.H0 * t) ** (2.0 / 3.0)
         y = self.H0 * t / self.B
@@ -64,10 +73,12 @@ class LambdaFree:
         return self.A * (math.cosh(u) - 1.0)
 
     def adot(self, t):
+        """da/dt = H0 a sqrt(Om / a^3 + (1 - Om) / a^2)."""
         a = self.a(t)
         return self.H0 * a * math.sqrt(self.Om / a**3 + (1.0 - self.Om) / a**2)
 
     def t_of_z(self, z):
+        """Time at redshift z."""
         a = 1.0 / (1.0 + z)
         if self.eds:
             return 2.0 / (3.0 * self.H0) * a**1.5

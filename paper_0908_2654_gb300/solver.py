@@ -105,11 +105,14 @@ class Solver:
 
     # ----------------------------------------------------------------- inputs
     def expansion(self, t):
+        """(a, da/dt) at time t [s]; (1, 0) for a static run."""
         if self.cosmo is None:
             return 1.0, 0.0
         return self.cosmo.a(t), self.cosmo.adot(t)
 
     def inputs(self, a=None, adot=None, dt=None):
+        """rt_step_inputs for a step of length dt [s] (default self.dt), a and adot at the
+        step's midpoint unless given; device pointers into this solver's tensors."""
         if a is None:
             a, adot = self.expansion(self.t + 0.5 * self.dt)
         dt = self.dt if dt is None else dt
@@ -127,6 +130,7 @@ class Solver:
         return s
 
     def state(self, E=None, nHI=None, ec=None, nHeI=None, nHeII=None):
+        """rt_state over the given normalised device tensors (default: the solver's own)."""
         st = _rt.State()
         st.E = _rt.ptr(self.E if E is None else E)
         st.n_HI = _rt.ptr(self.nHI if nHI is None else nHI)
@@ -233,6 +237,7 @@ class Solver:
 
     # ---------------------------------------------------------- kernel access
     def to_device(self, a, scale):
+        """A host array in CGS as a normalised FP64 device tensor (a / scale)."""
         return torch.as_tensor(np.ascontiguousarray(a / scale, dtype=np.float64)).to(self.dev)
 
     def residual(self, U_n, U, a=None, adot=None):
@@ -293,11 +298,13 @@ class Solver:
         return np.stack([t.cpu().numpy() * sc for t, sc in zip(out, scale)])
 
     def grey(self):
+        """The grey constants the library derived (CGS): sigma_E, sigma_G, eps_src."""
         vals = [ctypes.c_double() for _ in range(3)]
         _rt.check(_rt.lib().rt_grey_constants(self.handle, *[ctypes.byref(v) for v in vals]), "rt_grey_constants")
         return dict(sigma_E=vals[0].value, sigma_G=vals[1].value, eps_src=vals[2].value)
 
     def set_profiling(self, on):
+        """Enable (and reset) or disable the library's per-kernel event timing."""
         _rt.check(_rt.lib().rt_set_profiling(self.handle, int(on)), "rt_set_profiling")
 
     def profile(self):
@@ -309,6 +316,7 @@ class Solver:
                 for i in range(min(n.value, 32))}
 
     def close(self):
+        """Destroy the library grid (idempotent)."""
         if self.handle:
             _rt.lib().rt_destroy_grid(self.handle)
             self.handle = None

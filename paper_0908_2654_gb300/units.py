@@ -17,24 +17,30 @@ MYR = 3.15576e13
 
 @dataclass
 class Units:
+    """The three base units and the derived ones of Eqs. units and scalings."""
+
     u_x: float   # cm
     u_t: float   # s
     u_g: float   # g
 
     @property
     def u_d(self):
+        """Density unit u_g / u_x^3 [g/cm^3]."""
         return self.u_g / self.u_x**3
 
     @property
     def u_v(self):
+        """Velocity unit u_x / u_t [cm/s]."""
         return self.u_x / self.u_t
 
     @property
     def u_E(self):
+        """Radiation energy density unit u_d u_v^2 [erg/cm^3]."""
         return self.u_d * self.u_v**2
 
     @property
     def u_n(self):
+        """Number density unit u_d / m_H [1/cm^3]."""
         return self.u_d / M_H
 
     @staticmethod
@@ -58,6 +64,8 @@ def specific_energy(T, rho_b, nHI, v, helium=None):
 
 
 def temperature(e_total, rho_b, nHI, v):
+    """Temperature [K] of hydrogen-only gas (X = 1, n_tot = 2 n_H - n_HI) from its specific
+    total energy e_total [erg/g] and velocity v."""
     nH = rho_b / M_H
     e_int = e_total - 0.5 * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2)
     return (GAMMA - 1.0) * e_int * rho_b / (K_B * (2.0 * nH - nHI))
