@@ -52,3 +52,17 @@ def test_config_describes_the_workload_at_each_size():
         assert f"{n}^3, {nsrc} sources" in cfg["workload"]
         assert cfg["l2"].startswith("inputs larger than L2" if above else "inputs smaller than L2")
         assert bench.workload_sources(n) == nsrc
+
+
+def test_reference_arm_line(capsys):
+    """bench.py --impl reference: the oracle on host cores prints one JSON line with the
+    contract's keys, a cpu_baseline describing the run and a zero-copy e2e."""
+    args = argparse.Namespace(size=32, steps=1, warmup=0, newton_tol=1e-6, gpus=1)
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "cell-steps/s"
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] == 1
+    cpu = line["cpu_baseline"]
+    assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == line["value"] and cpu["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
