@@ -274,6 +274,16 @@ const char* rt_last_error_detail(void);
  * eps_src [erg] (Eq. grey_definition with sigma ~ nu^-3).  Errors: RT_EINVAL. */
 int rt_grey_constants(const rt_grid* g, double* sigma_E, double* sigma_G, double* eps_src);
 
+/* The same grey constants without a grid (host computation only, no CUDA call): for the
+ * spectrum (RT_SPECTRUM_MONO or RT_SPECTRUM_BLACKBODY at T_B kelvin, 0 < T_B < 1e9) it writes
+ * seven values to the host array out, in CGS:
+ *   [0] sigma_E [cm^2], [1] sigma_G [cm^2/erg], [2] eps_src [erg]  (hydrogen, as above);
+ *   [3] sigma_E,HeI, [4] sigma_G,HeI, [5] sigma_E,HeII, [6] sigma_G,HeII  (the helium grey
+ *   cross sections over the same spectrum, normalised by its energy above the hydrogen edge;
+ *   zero for the 13.6 eV line).
+ * Errors: RT_EINVAL. */
+int rt_spectrum_constants(int spectrum, double T_B, double* out);
+
 #ifdef __cplusplus
 }
 #endif

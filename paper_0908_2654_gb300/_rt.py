@@ -97,7 +97,8 @@ _lib = None
 EXPORTS = ["rt_init_grid", "rt_implicit_step", "rt_residual", "rt_schur_system", "rt_schur_solve",
            "rt_adjoint_step", "rt_fold_energy", "rt_destroy_grid", "rt_error_string",
            "rt_last_error_detail", "rt_grey_constants", "rt_set_profiling", "rt_get_profile",
-           "rt_residual_static", "rt_eval_elementary", "rt_advect", "rt_advect_adjoint", "rt_residual_helium"]
+           "rt_residual_static", "rt_eval_elementary", "rt_advect", "rt_advect_adjoint", "rt_residual_helium",
+           "rt_spectrum_constants"]
 
 
 def lib():
@@ -133,6 +134,7 @@ def lib():
     L.rt_eval_elementary.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]
     L.rt_residual_static.argtypes = [P(GridDesc), P(StepInputs), P(State), P(State)] + [ctypes.c_void_p] * 3
     L.rt_get_profile.argtypes = [ctypes.c_void_p, P(KernelProfile), ctypes.c_int, P(ctypes.c_int)]
+    L.rt_spectrum_constants.argtypes = [ctypes.c_int, ctypes.c_double, P(ctypes.c_double)]
     for name in EXPORTS:
         if name not in ("rt_destroy_grid", "rt_error_string", "rt_last_error_detail"):
             getattr(L, name).restype = ctypes.c_int

@@ -827,6 +827,19 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out) {
     return RT_OK;
 }
 
+int rt_spectrum_constants(int spectrum, double T_B, double* out) {
+    if (!out || (spectrum != RT_SPECTRUM_MONO && spectrum != RT_SPECTRUM_BLACKBODY) ||
+        (spectrum == RT_SPECTRUM_BLACKBODY && !(T_B > 0.0 && T_B < 1e9))) {
+        set_detail("rt_spectrum_constants needs an output array and a known spectrum with 0 < T_B < 1e9 K");
+        return RT_EINVAL;
+    }
+    const Grey g = grey_constants(spectrum, T_B);
+    const GreyHe h = helium_grey_constants(spectrum, T_B);
+    const double v[7] = {g.sigma_E, g.sigma_G, g.eps_src, h.sE1, h.sG1, h.sE2, h.sG2};
+    for (int k = 0; k < 7; ++k) out[k] = v[k];
+    return RT_OK;
+}
+
 int rt_grey_constants(const rt_grid* g, double* sigma_E, double* sigma_G, double* eps_src) {
     if (!g) {
         set_detail("null grid");

@@ -173,3 +173,29 @@ def test_static_residual_limits(L):
     bad_theta = _desc(nx=2, ny=2, nz=2, theta=2.0)
     assert L.rt_residual_static(ctypes.byref(bad_theta), ctypes.byref(inp), ctypes.byref(st), ctypes.byref(st),
                                 p, p, p) == _rt.RT_EINVAL
+
+
+@pytest.mark.parametrize("spectrum,T_B", [("mono", 1e5), ("blackbody", 1e4), ("blackbody", 3e4), ("blackbody", 1e5),
+                                          ("blackbody", 3e5), ("blackbody", 1e6)])
+def test_library_grey_constants_match_oracle(L, spectrum, T_B):
+    """The library's own host quadrature of the grey constants (Eq. grey_definition, composite
+    Gauss-Legendre) against the oracle's adaptive quadrature, hydrogen and helium, through
+    rt_spectrum_constants (no CUDA call)."""
+    from oracle import spectrum as S
+    out = (ctypes.c_double * 7)()
+    code = _rt.RT_SPECTRUM_MONO if spectrum == "mono" else _rt.RT_SPECTRUM_BLACKBODY
+    assert L.rt_spectrum_constants(code, T_B, out) == _rt.RT_OK
+    h = S.grey_constants(spectrum, T_B)
+    he = S.helium_grey_constants(spectrum, T_B)
+    ref = [h["sigma_E"], h["sigma_G"], h["eps_src"], he["sigma_E_HeI"], he["sigma_G_HeI"], he["sigma_E_HeII"],
+           he["sigma_G_HeII"]]
+    for k, (got, want) in enumerate(zip(out, ref)):
+        assert got == pytest.approx(want, rel=1e-11, abs=0.0), k
+
+
+def test_spectrum_constants_arguments(L):
+    out = (ctypes.c_double * 7)()
+    assert L.rt_spectrum_constants(7, 1e5, out) == _rt.RT_EINVAL
+    assert L.rt_spectrum_constants(_rt.RT_SPECTRUM_BLACKBODY, 0.0, out) == _rt.RT_EINVAL
+    assert L.rt_spectrum_constants(_rt.RT_SPECTRUM_BLACKBODY, nan, out) == _rt.RT_EINVAL
+    assert L.rt_spectrum_constants(_rt.RT_SPECTRUM_BLACKBODY, 1e5, None) == _rt.RT_EINVAL
