@@ -182,18 +182,23 @@ def test_diffusion_conserves_energy_with_walls_and_periodic():
         assert abs(Ld.sum()) <= 1e-12 * np.abs(Ld).sum()
 
 
-def test_absorption_of_uniform_field_matches_scalar_root():
-    """Uniform gas and field: the step reduces to one scalar equation in E (brentq root)."""
+@pytest.mark.parametrize("n,src", [((4, 3, 3), 4e-31), ((4, 3, 3), 0.0), ((1, 1, 5), 4e-31), ((2, 2, 2), 0.0),
+                                   ((5, 1, 1), 4e-31)])
+def test_absorption_of_uniform_field_matches_scalar_root(n, src):
+    """Uniform gas and field: the step reduces to one scalar equation in E (brentq root), also
+    with no sources and on the degenerate grids (one-cell-thin, 2^3)."""
     g = S.grey_constants("blackbody", 1e5)
     a, adot, dt, theta = 0.25, 1e-17, 2e13, 0.8
-    nH, En, nHIn, src = 2e-4, 3e-16, 2e-8, 4e-31
-    n = (4, 3, 3)
+    nH, En, nHIn = 2e-4, 3e-16, 2e-8
     shape = (n[2], n[1], n[0])
+    # axes under 3 cells get zero-flux walls (the oracle's periodic Jacobian colouring needs 3);
+    # a uniform field stays uniform either way
     st = _uniform_step(n, a=a, adot=adot, dt=dt, theta=theta, rho_b=np.full(shape, nH * K.M_H),
-                       E_n=np.full(shape, En), nHI_n=np.full(shape, nHIn), **g)
-    # a uniform emissivity written as one source per cell
-    st.src_index = np.arange(st.N)
-    st.src_ndot = np.full(st.N, src * st.dx**3 / g["eps_src"])
+                       E_n=np.full(shape, En), nHI_n=np.full(shape, nHIn),
+                       periodic=tuple(nd >= 3 for nd in n), **g)
+    # a uniform emissivity written as one source per cell (none when src = 0)
+    st.src_index = np.arange(st.N) if src > 0 else np.zeros(0, np.int64)
+    st.src_ndot = np.full(st.N, src * st.dx**3 / g["eps_src"]) if src > 0 else np.zeros(0)
     U, _ = N.solve_step(st, tol=1e-13)
 
     def Sn(E):
