@@ -172,6 +172,37 @@ def test_fourier_mode_amplification_is_exact():
     np.testing.assert_allclose(U[2], expect, rtol=1e-11)
 
 
+@pytest.mark.parametrize("theta", [0.51, 1.0])
+def test_gaussian_spreading_variance_law(theta):
+    """Constant-D diffusion of a Gaussian pulse, no opacity or expansion: the pulse's energy
+    is conserved and its variance grows as sigma^2(t) = sigma_0^2 + 2 D t along the axis of
+    the pulse.  For the discrete theta-scheme this holds exactly, step by step: summing
+    x^2 times the 7-point Laplacian by parts gives 2 (a dx)^2 times the energy, at either
+    time level, while the pulse stays clear of the periodic wrap (the implicit scheme's tails,
+    geometric rather than Gaussian, are below 1e-16 of the peak there).  A wrong Laplacian weight, theta split or 1/a^2 changes the growth."""
+    n = (64, 3, 3)
+    a, dt, Dc, dx = 0.5, 2e13, 2e28, 3e21
+    x = np.arange(n[0]) - 31.5
+    sig0 = 1.6                                           # cells
+    prof = np.exp(-0.5 * (x / sig0) ** 2)
+    En = 1e-20 * np.broadcast_to(prof, (n[2], n[1], n[0])).copy()
+    st = _uniform_step(n, E_n=En, a=a, adot=0.0, dt=dt, dx=dx, theta=theta, limiter="const", D_const=Dc)
+    steps, E = 3, En
+    for _ in range(steps):
+        st.E_n = E
+        U, _ = N.solve_step(st, tol=1e-14)
+        E = U[2]
+    ex = E.sum(axis=(0, 1))                              # profile along x
+    m0_0, m0 = En.sum(axis=(0, 1)).sum(), ex.sum()
+    var0 = float(np.sum(En.sum(axis=(0, 1)) * x**2) / m0_0)
+    var = float(np.sum(ex * x**2) / m0)
+    growth = 2.0 * Dc * steps * dt / (a * dx) ** 2      # cells^2
+    assert m0 == pytest.approx(m0_0, rel=1e-12)
+    assert var - var0 == pytest.approx(growth, rel=1e-9)
+    assert 0.5 < growth < 4.0                            # a real spread, far from the wrap
+    assert ex[0] < 1e-16 * ex.max() and ex[-1] < 1e-16 * ex.max()
+
+
 def test_diffusion_conserves_energy_with_walls_and_periodic():
     rng = np.random.default_rng(3)
     for periodic in ((True, True, True), (False, True, False)):
