@@ -54,3 +54,23 @@ def test_binding_loads_and_error_strings(libpath):
     hdr = open(HEADER).read()
     for field in ("newton_tol", "lin_rtol", "mg_nu1", "stream"):
         assert field in hdr and field in [f for f, _ in _rt.GridDesc._fields_]
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without the built library the binding raises instead of computing."""
+    from paper_0908_2654_gb300 import _rt
+    monkeypatch.setattr(_rt, "LIB_PATH", str(tmp_path / "librtfld.so"))
+    monkeypatch.setattr(_rt, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        _rt.lib()
+
+
+def test_solver_without_a_gpu_raises():
+    """On a machine without a GPU the solver refuses to run (no CPU path exists)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import workloads as W
+    from paper_0908_2654_gb300.solver import Solver
+    with pytest.raises(Exception):
+        Solver(W.stromgren_static(n=8), precision="fp64")
