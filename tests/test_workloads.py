@@ -93,3 +93,42 @@ def test_ionised_blocks_around_sources(field):
     np.testing.assert_allclose(xHI[blocks], 1e-4, rtol=1e-12)
     np.testing.assert_allclose(xHI[~blocks], 0.9999, rtol=1e-12)
     assert np.all(field["T0"][blocks] == 1e4) and np.all(field["T0"][~blocks] == 100.0)
+
+
+def _gold():
+    import json
+    import os
+    return json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def test_stromgren_workloads_use_the_papers_values():
+    """Static and cosmological Stromgren inputs: the paper's source rate, initial radiation
+    energy, case-B coefficient and 1e4 K isothermal gas, the source in the octant corner
+    emitting Ndot / 8, walls on every axis, and t_rec = 1 / (alpha_B n_H)."""
+    gold = _gold()
+    ndot, E0, alpha = (gold[k]["value"] for k in ("Ndot_photons_s", "E_initial_erg_cm3", "alpha_B_cm3_s"))
+    for w in (W.stromgren_static(n=8), W.stromgren_cosmo(n=8)):
+        assert w["ndot_total"] == ndot and np.all(w["src_ndot"] == ndot / 8.0)
+        assert list(w["src_index"]) == [0] and w["octant"] and w["periodic"] == (False, False, False)
+        assert np.all(w["E"] == E0) and np.all(w["T0"] == 1e4)
+        assert w["isothermal"] and w["T_iso"] == 1e4 and w["recomb"] == "const"
+    w = W.stromgren_static(n=8)
+    assert w["t_rec"] == pytest.approx(1.0 / (alpha * 1e-3), rel=1e-15)
+    assert w["dt"] == pytest.approx(0.01 * w["t_rec"], rel=1e-15)
+    assert w["dx"] * w["nx"] == pytest.approx(6.6 * 3.0856775814913673e21, rel=1e-15)
+
+
+@pytest.mark.parametrize("row", range(4))
+def test_shapiro_giroux_inputs_follow_table1(row):
+    """Table 1 row by row: the generator's table is the paper's, the box is L0 comoving at z0
+    (proper L0 at z0), the gas is Omega_b rho_crit, comoving, fully neutral, and the source
+    is the paper's monochromatic 13.6 eV one."""
+    gold = _gold()
+    q0, z0, L0, h, Om, OL, Ob = gold["table1"]["rows"][row]
+    assert tuple(float(v) for v in W.SG_TABLE1[row]) == tuple(float(v) for v in (q0, z0, L0, h, Om, OL, Ob))
+    w = W.shapiro_giroux(row, n=8)
+    assert w["dx"] * w["nx"] / (1.0 + z0) == pytest.approx(L0 * 3.0856775814913673e21, rel=1e-15)
+    nH = Ob * W.RHO_CRIT_H2 * h**2 / W.M_H
+    np.testing.assert_allclose(w["rho_b"], nH * W.M_H, rtol=1e-15)
+    np.testing.assert_allclose(w["nHI"], nH, rtol=1e-15)
+    assert w["spectrum"] == "mono" and w["cosmology"] == dict(q0=q0, h=h) and w["z0"] == z0
