@@ -7,7 +7,9 @@ documented dtype; their device pointers go straight to the library.
 import ctypes
 import os
 
-import torch
+# imported before the library is loaded: the process's CUDA runtime is then the one PyTorch
+# loads, and the library binds to that same libcudart
+import torch  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "librtfld.so")

@@ -12,7 +12,7 @@ import torch
 
 from . import _rt
 from .cosmology import from_dict as cosmology_from_dict
-from .units import MYR, Units, specific_energy
+from .units import Units, specific_energy
 
 _SPECTRA = {"mono": _rt.RT_SPECTRUM_MONO, "blackbody": _rt.RT_SPECTRUM_BLACKBODY}
 _RECOMB = {"const": _rt.RT_RECOMB_CONST, "hg97": _rt.RT_RECOMB_HG97}

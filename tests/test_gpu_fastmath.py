@@ -1,7 +1,6 @@
 """The table-driven FP64 exp and log used by the rate fits against NumPy (glibc) and the CUDA
 math library: at most 2 units in the last place over the ranges the rates use and beyond,
 and the special values."""
-import ctypes
 
 import numpy as np
 import pytest

@@ -8,7 +8,6 @@
 * Error paths: invalid shapes and sources, non-finite input, too few Newton iterations;
   the caller's state must be untouched on error.
 """
-import math
 
 import numpy as np
 import pytest

@@ -12,7 +12,6 @@ Tolerances:
     the stopping test.  The benchmark spec's bound of 1e-10 relative holds on every
     cell whose E is above the floor (checked separately).
 """
-import math
 
 import numpy as np
 import pytest
