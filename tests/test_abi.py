@@ -74,3 +74,26 @@ def test_solver_without_a_gpu_raises():
     from paper_0908_2654_gb300.solver import Solver
     with pytest.raises(Exception):
         Solver(W.stromgren_static(n=8), precision="fp64")
+
+
+def test_ctypes_mirrors_match_the_c_struct_layouts(tmp_path):
+    """Every struct of include/rt.h has, in the Python binding, the same size and the same
+    offset for every field (compiled with the host C compiler)."""
+    import json
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    exe = str(tmp_path / "abi_layout")
+    subprocess.run([cc, "-std=c99", "-o", exe, os.path.join(ROOT, "tests", "host", "abi_layout.c")], check=True)
+    layout = json.loads(subprocess.run([exe], capture_output=True, text=True, check=True).stdout)
+    from paper_0908_2654_gb300 import _rt
+    mirrors = {"rt_grid_desc": _rt.GridDesc, "rt_step_inputs": _rt.StepInputs, "rt_state": _rt.State,
+               "rt_step_stats": _rt.StepStats, "rt_kernel_profile": _rt.KernelProfile}
+    for cname, py in mirrors.items():
+        c = layout[cname]
+        assert ctypes.sizeof(py) == c["__size__"], cname
+        fields = [f for f, _ in py._fields_]
+        assert sorted(fields) == sorted(k for k in c if not k.startswith("__")), cname
+        for f in fields:
+            assert getattr(py, f).offset == c[f], (cname, f)
