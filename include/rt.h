@@ -147,9 +147,10 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out);
 /* One implicit step (v): on entry *inout holds the advected state (E*, n_HI*, and n_HeI*,
  * n_HeII* on helium grids; e_c is ignored and taken as 0), on success it holds U^{n+1} with
  * f(U^{n+1}) below newton_tol.
- * stats may be NULL; it describes the attempt on success and on RT_ENOCONV, RT_ELINESEARCH and
- * linear-solver failures, and is left as the caller passed it on argument errors, RT_ECUDA and
- * RT_ENONFINITE.  Errors: RT_EINVAL, RT_ENOCONV, RT_ELINESEARCH, RT_ENONFINITE, RT_ELINEAR,
+ * stats may be NULL.  It describes the attempt on success, on RT_ENOCONV and RT_ELINESEARCH,
+ * and on any error the linear solve returns.  It is left as the caller passed it on argument
+ * errors, on a non-finite residual evaluation and on CUDA errors outside the linear solve.
+ * Errors: RT_EINVAL, RT_ENOCONV, RT_ELINESEARCH, RT_ENONFINITE, RT_ELINEAR,
  * RT_ECUDA; *inout is unchanged on error. */
 int rt_implicit_step(rt_grid* g, const rt_step_inputs* in, rt_state* inout, rt_step_stats* stats);
 
