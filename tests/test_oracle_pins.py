@@ -203,6 +203,32 @@ def test_gaussian_spreading_variance_law(theta):
     assert ex[0] < 1e-16 * ex.max() and ex[-1] < 1e-16 * ex.max()
 
 
+def test_gaussian_spreading_converges_at_second_order():
+    """The discrete solution of constant-D diffusion converges to the continuum Gaussian
+    E = A sigma0 / sigma(t) exp(-x^2 / (2 sigma(t)^2)), sigma^2 = sigma0^2 + 2 D t, at second
+    order.  The test uses Crank-Nicolson (theta = 1/2), halves dx and dt together, and checks
+    that the max-norm error falls by about 4 at each refinement."""
+    L, a, Dc = 48 * 3e21, 1.0, 2e28
+    sig0 = L / 48 * 2.5                                   # 2.5 coarse cells
+    t_end = 0.5 * sig0**2 / Dc                            # sigma^2 doubles
+    errs = []
+    for n, nsteps in ((48, 4), (96, 8), (192, 16)):
+        dx = L / n
+        x = (np.arange(n) + 0.5) * dx - 0.5 * L
+        gauss = lambda t: np.exp(-x**2 / (2 * (sig0**2 + 2 * Dc * t))) * sig0 / np.sqrt(sig0**2 + 2 * Dc * t)
+        En = 1e-20 * np.broadcast_to(gauss(0.0), (3, 3, n)).copy()
+        st = _uniform_step((n, 3, 3), E_n=En, a=a, adot=0.0, dt=t_end / nsteps, dx=dx, theta=0.5,
+                           limiter="const", D_const=Dc)
+        E = En
+        for _ in range(nsteps):
+            st.E_n = E
+            U, _ = N.solve_step(st, tol=1e-14)
+            E = U[2]
+        errs.append(np.max(np.abs(E[1, 1] / 1e-20 - gauss(t_end))))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.5 < r1 < 4.5 and 3.7 < r2 < 4.3, (errs, r1, r2)
+
+
 def test_diffusion_conserves_energy_with_walls_and_periodic():
     rng = np.random.default_rng(3)
     for periodic in ((True, True, True), (False, True, False)):
