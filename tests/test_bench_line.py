@@ -1,9 +1,11 @@
-"""bench.py's JSON line assembled from fake GPU results on the CPU: every key the output
-contract asks for, the roofline arithmetic of the dominant kernel and of the smoother (all
-levels and the fine level alone), and that the line serialises."""
+"""bench.py on the CPU: the JSON line assembled from fake GPU results, with every key the
+output contract asks for, the roofline arithmetic of the dominant kernel and of the smoother
+(all levels and the fine level alone), and that the line serialises; the reference arm's
+line; the mixed-vs-FP64 error definitions and the oracle's sub-block sampling."""
 import argparse
 import json
 
+import numpy as np
 import pytest
 
 import bench
@@ -66,3 +68,40 @@ def test_reference_arm_line(capsys):
     assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == line["value"] and cpu["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_state_errors_definitions():
+    """E normwise (2 and max) relative, x_HI pointwise relative with a 1e-8 floor, T pointwise."""
+    Eb, xb, Tb = np.array([1.0, 2.0, 2.0]), np.array([1e-10, 0.5, 1.0]), np.array([100.0, 1e4, 1e4])
+    Ea, xa, Ta = Eb + np.array([0.0, 0.0, 0.3]), xb + np.array([1e-9, 0.0, -0.1]), Tb * np.array([1.0, 1.01, 1.0])
+    e = bench.state_errors((Ea, xa, Ta), (Eb, xb, Tb))
+    assert e["E_rel_2"] == pytest.approx(0.3 / 3.0)
+    assert e["E_rel_inf"] == pytest.approx(0.3 / 2.0)
+    assert e["xHI_rel_max"] == pytest.approx(0.1)          # 1e-9 / max(1e-10, 1e-8) = 0.1 as well
+    assert e["T_rel_max"] == pytest.approx(0.01)
+
+
+def test_oracle_sample_is_the_sub_block_with_its_sources():
+    import workloads as W
+    w = W.reionization_field(n=16, nsrc=12, box_mpc=14.4 * 16 / 256)
+    m = 8
+    corner = bench.densest_corner(w, m)
+    shape = (16, 16, 16)
+    zc, yc, xc = np.unravel_index(w["src_index"], shape)
+    counts = {}
+    for z0 in (0, 8):
+        for y0 in (0, 8):
+            for x0 in (0, 8):
+                counts[(z0, y0, x0)] = int(np.sum((zc // 8 == z0 // 8) & (yc // 8 == y0 // 8) & (xc // 8 == x0 // 8)))
+    assert counts[corner] == max(counts.values())
+    sub = bench.oracle_sample(w, m, corner)
+    z0, y0, x0 = corner
+    np.testing.assert_array_equal(sub["rho_b"], w["rho_b"][z0:z0 + m, y0:y0 + m, x0:x0 + m])
+    assert sub["nx"] == sub["ny"] == sub["nz"] == m and sub["periodic"] == (True, True, True)
+    assert len(sub["src_index"]) == counts[corner]
+    # each sub-block source is the same cell, with the same rate, as in the full field
+    sz, sy, sx = np.unravel_index(sub["src_index"], (m, m, m))
+    full = np.ravel_multi_index((sz + z0, sy + y0, sx + x0), shape)
+    for f, nd in zip(full, sub["src_ndot"]):
+        k = int(np.flatnonzero(np.asarray(w["src_index"]) == f)[0])
+        assert nd == w["src_ndot"][k]
