@@ -205,17 +205,22 @@ int rt_residual_helium(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n
 int rt_eval_elementary(int fn, const double* x, double* y, long long n, void* stream);
 
 /* Allocation-free residual.  The paper has no counterpart: this is a service for callers
- * that cannot allocate device memory (an application that owns the whole device memory
- * budget through its own pool, work issued during CUDA stream capture, allocation-free
- * real-time loops).  It computes the same f(U) as rt_residual but takes the descriptor
- * instead of a grid handle and calls no cudaMalloc, cudaFree or allocating library routine:
- * its scratch is one file-scope device array of RT_RESIDUAL_STATIC_MAX_CELLS cells' worth
- * (about 2.2 MB), which every GPU that loads the library holds until the process exits.
- * Grids with more cells are rejected with RT_EINVAL.  The first call on a device looks up
- * the array's device address on that device; make that first call before any stream
- * capture.  Every call uses the same array: calls whose GPU work overlaps (other streams,
- * other host threads on the same device) race on it and must be serialised by the caller.
- * Arguments as rt_residual; desc->device and desc->stream select where the work runs.
+ * that cannot allocate device memory -- an application that owns the whole device memory
+ * budget through its own pool allocator (a library's own cudaMalloc there fails or fragments
+ * that budget), or a real-time loop that must not take the device-wide synchronisation
+ * cudaMalloc and cudaFree may cause.  It computes the same f(U) as rt_residual but takes the
+ * descriptor instead of a grid handle and calls no cudaMalloc, cudaFree or allocating library
+ * routine: its scratch is one file-scope device array of RT_RESIDUAL_STATIC_MAX_CELLS cells'
+ * worth (about 2.2 MB), which every GPU that loads the library holds until the process exits.
+ * Grids with more cells are rejected with RT_EINVAL, as are device ordinals outside 0..63.
+ * The first call on a device looks up the array's device address on that device (and caches
+ * it); make that first call before any stream capture, and make no call after a
+ * cudaDeviceReset of that device.  Every call uses the same array and it keeps the last
+ * call's contents: calls whose GPU work overlaps (other streams, other host threads on the
+ * same device) race on it and must be serialised by the caller.
+ * Arguments as rt_residual; desc->device and desc->stream select where the work runs; the
+ * calling thread's current device is restored before the call returns.  The call returns
+ * after synchronising desc->stream.  Hydrogen-only grids.
  * Errors: RT_EINVAL, RT_ECUDA. */
 #define RT_RESIDUAL_STATIC_MAX_CELLS 32768
 int rt_residual_static(const rt_grid_desc* desc, const rt_step_inputs* in, const rt_state* U_n,

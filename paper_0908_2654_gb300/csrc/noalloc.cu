@@ -1,11 +1,11 @@
 // rt_residual_static: the residual evaluation of rt_residual for callers that cannot allocate
 // device memory.  Some callers run where cudaMalloc is not available to them: code embedded in
-// a larger application that owns the whole device memory budget through its own pool, code
-// issued while a stream is being captured into a CUDA graph, or allocation-free real-time
-// loops.  This entry point needs no grid handle (rt_init_grid allocates its workspace) and
-// calls no cudaMalloc, cudaFree or allocating library routine.  Its scratch memory is the
-// file-scope device array below, which every GPU that loads the library keeps until the
-// process exits.
+// a larger application that owns the whole device memory budget through its own pool (a
+// library's own cudaMalloc there fails or fragments that budget), or real-time loops that
+// forbid the device-wide synchronisation cudaMalloc and cudaFree may cause.  This entry point
+// needs no grid handle (rt_init_grid allocates its workspace) and calls no cudaMalloc,
+// cudaFree or allocating library routine.  Its scratch memory is the file-scope device array
+// below, which every GPU that loads the library keeps until the process exits.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -35,9 +35,9 @@ double* g_scratch_addr[kMaxDevices] = {};   // device address of g_scratch, per 
 
 // The address of g_scratch on the current device.  In host code the name g_scratch is only a
 // host-side stand-in, so the device address is looked up once per device with that device
-// current.
+// current (the first call on the device) and cached; the cache is not refreshed after a
+// cudaDeviceReset, so calls after a reset are not supported.
 int scratch_for_device(int dev, double** out) {
-    if (dev < 0 || dev >= kMaxDevices) return RT_EINVAL;
     std::lock_guard<std::mutex> lock(g_mutex);
     if (!g_scratch_addr[dev]) {
         void* p = nullptr;
@@ -50,6 +50,9 @@ int scratch_for_device(int dev, double** out) {
     *out = g_scratch_addr[dev];
     return RT_OK;
 }
+
+int residual_on_device(const rt_grid_desc* desc, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U,
+                       double* f_e, double* f_n, double* f_E, const PhysParams& P);
 
 }  // namespace
 
@@ -69,15 +72,38 @@ extern "C" int rt_residual_static(const rt_grid_desc* desc, const rt_step_inputs
         rt_internal_set_detail("rt_residual_static takes at most RT_RESIDUAL_STATIC_MAX_CELLS cells");
         return RT_EINVAL;
     }
+    if (desc->device < 0 || desc->device >= kMaxDevices) {
+        rt_internal_set_detail("rt_residual_static: device ordinal outside 0..63");
+        return RT_EINVAL;
+    }
     PhysParams P;
     int rc = rt_internal_step_params(desc, in, &P);
     if (rc) return rc;
+    // the caller's current device is put back before returning
+    int prev_dev = 0;
+    if (cudaGetDevice(&prev_dev) != cudaSuccess) {
+        rt_internal_set_detail("cudaGetDevice failed");
+        return RT_ECUDA;
+    }
     if (cudaSetDevice(desc->device) != cudaSuccess) {
         rt_internal_set_detail("cudaSetDevice failed");
         return RT_ECUDA;
     }
+    rc = residual_on_device(desc, in, U_n, U, f_e, f_n, f_E, P);
+    if (cudaSetDevice(prev_dev) != cudaSuccess && rc == RT_OK) {
+        rt_internal_set_detail("cudaSetDevice could not restore the caller's device");
+        rc = RT_ECUDA;
+    }
+    return rc;
+}
+
+namespace {
+
+int residual_on_device(const rt_grid_desc* desc, const rt_step_inputs* in, const rt_state* U_n, const rt_state* U,
+                       double* f_e, double* f_n, double* f_E, const PhysParams& P) {
+    const long long n = (long long)desc->nx * desc->ny * desc->nz;
     double* base = nullptr;
-    rc = scratch_for_device(desc->device, &base);
+    int rc = scratch_for_device(desc->device, &base);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)desc->stream;
     double* src = base;
@@ -137,3 +163,5 @@ extern "C" int rt_residual_static(const rt_grid_desc* desc, const rt_step_inputs
     }
     return RT_OK;
 }
+
+}  // namespace
