@@ -345,7 +345,7 @@ def oracle_sample(w, m, seed_corner=(0, 0, 0)):
     zc, yc, xc = np.unravel_index(w["src_index"], shape)
     inside = (zc >= z0) & (zc < z0 + m) & (yc >= y0) & (yc < y0 + m) & (xc >= x0) & (xc < x0 + m)
     sub = dict(w)
-    sub.update(nx=m, ny=m, nz=m, periodic=(True, True, True),
+    sub.update(nx=m, ny=m, nz=m, periodic=(True, True, True), bc=None,
                rho_b=w["rho_b"][sl].copy(), T0=w["T0"][sl].copy(), v=tuple(v[sl].copy() for v in w["v"]),
                clump=w["clump"][sl].copy(), E=w["E"][sl].copy(), nHI=w["nHI"][sl].copy(),
                src_index=np.ravel_multi_index((zc[inside] - z0, yc[inside] - y0, xc[inside] - x0), (m, m, m)),

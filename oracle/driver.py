@@ -73,7 +73,7 @@ class Run:
         if a is None:
             a, adot = expansion(w, self.t + 0.5 * self.dt)
         return M.Step(
-            nx=w["nx"], ny=w["ny"], nz=w["nz"], dx=w["dx"], periodic=w["periodic"],
+            nx=w["nx"], ny=w["ny"], nz=w["nz"], dx=w["dx"], periodic=w["periodic"], bc=w.get("bc"),
             rho_b=self.rho_b, e_h=self.e_h, v=w["v"], clump=np.asarray(w["clump"], float),
             E_n=self.E, nHI_n=self.nHI, a=a, adot=adot, dt=self.dt if dt is None else dt,
             src_index=w["src_index"], src_ndot=w["src_ndot"],

@@ -36,9 +36,15 @@ Readings of points the paper leaves open (listed in the design notes):
   * S_e: exact solution of de/dt = -2 (adot/a) e + (G - Lambda) with frozen
     G - Lambda and e_c^n = 0; isothermal runs use f_e = e_c.
   * Point sources: 4 pi eta = sum_s Ndot_s eps_src / dx^3 in the source's cell.
+  * Boundaries (Sec. "Verification tests": reflecting at the lower faces, outflow at the upper
+    faces), per face: "periodic" (both faces of the axis), "reflect" (zero flux through the
+    face) or "outflow".  Outflow lets radiation leave the box: beyond the face lies a ghost
+    cell holding no radiation (E = 0) and a copy of the boundary cell's gas (same opacity), and
+    the face flux follows Eq. limiter between the two like any interior face.  (A ghost holding
+    a copy of E as well would give zero diffusive flux, i.e. a reflecting face.)
 """
 from dataclasses import dataclass, field
-from typing import Tuple
+from typing import Optional, Tuple
 
 import numpy as np
 
@@ -74,7 +80,7 @@ class Step:
     ny: int
     nz: int
     dx: float                                   # comoving cell width [cm]
-    periodic: Tuple[bool, bool, bool]           # (x, y, z); False = zero-flux walls
+    periodic: Tuple[bool, bool, bool]           # (x, y, z); False = see bc (default: reflect)
     rho_b: np.ndarray                           # comoving baryon density [g/cm^3]
     e_h: np.ndarray                             # specific total gas energy after hydro [erg/g]
     v: Tuple[np.ndarray, np.ndarray, np.ndarray]  # proper peculiar velocity (x, y, z) [cm/s]
@@ -97,6 +103,20 @@ class Step:
     limiter: str = "lagged"                     # "lagged" | "new" | "const"
     D_const: float = 0.0                        # proper diffusion coefficient for limiter "const"
     E_min: float = E_MIN_DEFAULT
+    bc: Optional[Tuple[str, ...]] = None        # per face (x-, x+, y-, y+, z-, z+); None: from periodic
+
+    @property
+    def faces(self):
+        """Boundary type of the six faces (x-, x+, y-, y+, z-, z+): "periodic", "reflect" or
+        "outflow"; without ``bc`` the non-periodic axes reflect at both faces."""
+        if self.bc is not None:
+            bc = tuple(self.bc)
+            for d in range(3):
+                per = (bc[2 * d] == "periodic", bc[2 * d + 1] == "periodic")
+                if per != (bool(self.periodic[d]),) * 2:
+                    raise ValueError(f"boundary types {bc} disagree with periodic={self.periodic}")
+            return bc
+        return tuple(t for p in self.periodic for t in (("periodic",) * 2 if p else ("reflect",) * 2))
 
     @property
     def shape(self):
@@ -125,50 +145,92 @@ def limiter_D(kappa_T, R):
 _AXIS = {0: 2, 1: 1, 2: 0}   # (x, y, z) -> numpy axis of an [z, y, x] array
 
 
-def face_D(st, E, kappa, d, freeze=False):
-    """D on the +d face of every cell (face between cell i and its +d neighbour).
+def _limiter_faces(st, E, Ep, kappa, kp):
+    """Eq. limiter on faces between cells with energies (E, Ep) and proper opacities (kappa, kp):
+    R = |Ep - E| / (a dx pos(mean E)), kappa_T the mean opacity, R = 1/(a dx) where both vanish."""
+    adx = st.a * st.dx
+    if st.limiter == "const":
+        return np.full(np.shape(E), st.D_const, dtype=np.result_type(E, float))
+    Ef = spos(0.5 * (E + Ep), st.E_min)
+    R = cabs(Ep - E) / (adx * Ef)
+    kT = 0.5 * (kappa + kp)
+    both0 = (np.real(kT) == 0) & (np.real(R) == 0)
+    R = np.where(both0, 1.0 / adx, R)
+    return limiter_D(kT, R)
 
-    Returns the array; the face of the last cell along a non-periodic axis is a
-    wall and is given D = 0 (no flux).  Limiter "lagged" evaluates D from the
-    step's starting state (E^n, kappa^n) at both time levels; "new" from the
-    iterate (E, kappa), and with freeze=True from its real parts only (a
-    linearisation that holds D fixed); "const" uses D_const.
-    """
-    ax = _AXIS[d]
+
+def _limiter_state(st, E, kappa, freeze):
+    """(E, kappa) the limiter is evaluated from: the step's start for limiter "lagged"."""
     if st.limiter == "lagged":
         E, kappa = st.E_n, opacity(st, st.nHI_n)
     if freeze:
         E = np.real(E)
         kappa = np.real(kappa)
-    Ep = np.roll(E, -1, axis=ax)
-    kp = np.roll(kappa, -1, axis=ax)
-    adx = st.a * st.dx
-    if st.limiter == "const":
-        D = np.full(st.shape, st.D_const, dtype=np.result_type(E, float))
-    else:
-        Ef = spos(0.5 * (E + Ep), st.E_min)
-        R = cabs(Ep - E) / (adx * Ef)
-        kT = 0.5 * (kappa + kp)
-        both0 = (np.real(kT) == 0) & (np.real(R) == 0)
-        R = np.where(both0, 1.0 / adx, R)
-        D = limiter_D(kT, R)
+    return E, kappa
+
+
+def face_D(st, E, kappa, d, freeze=False):
+    """D on the +d face of every cell (face between cell i and its +d neighbour).
+
+    Limiter "lagged" evaluates D from the step's starting state (E^n, kappa^n) at both time
+    levels; "new" from the iterate (E, kappa), and with freeze=True from its real parts only
+    (a linearisation that holds D fixed); "const" uses D_const.  On the last cell along a
+    non-periodic axis the +d face is the boundary: D = 0 for a reflecting face; for an outflow
+    face D is the limiter between the cell and its ghost (E = 0, the cell's own opacity).
+    """
+    ax = _AXIS[d]
+    E, kappa = _limiter_state(st, E, kappa, freeze)
+    D = _limiter_faces(st, E, np.roll(E, -1, axis=ax), kappa, np.roll(kappa, -1, axis=ax))
     if not st.periodic[d]:
-        idx = [slice(None)] * 3
-        idx[ax] = -1
+        last = [slice(None)] * 3
+        last[ax] = -1
+        last = tuple(last)
         D = D.copy()
-        D[tuple(idx)] = 0.0
+        if st.faces[2 * d + 1] == "outflow":
+            D[last] = _limiter_faces(st, E[last], 0.0 * E[last], kappa[last], kappa[last])
+        else:
+            D[last] = 0.0
     return D
 
 
+def lower_boundary_D(st, E, kappa, d, freeze=False):
+    """D on the -d boundary face of the first cell along a non-periodic axis (an [..] slab of
+    the array's shape with that axis of length 1): the limiter between the cell and its ghost
+    for an outflow face, 0 for a reflecting one."""
+    ax = _AXIS[d]
+    E, kappa = _limiter_state(st, E, kappa, freeze)
+    first = [slice(None)] * 3
+    first[ax] = slice(0, 1)
+    first = tuple(first)
+    if st.faces[2 * d] == "outflow":
+        return _limiter_faces(st, E[first], 0.0 * E[first], kappa[first], kappa[first])
+    return np.zeros(np.shape(E[first]), dtype=np.result_type(E, float))
+
+
 def diffusion(st, E, kappa, freeze=False):
-    """div(D grad E) with proper spacing a*dx: sum over faces of D (E_nb - E) / (a dx)^2."""
+    """div(D grad E) with proper spacing a*dx: sum over the cell's faces of D (E_nb - E) / (a dx)^2,
+    where the neighbour beyond an outflow face is the ghost E = 0 and a reflecting face carries
+    no flux."""
     adx2 = (st.a * st.dx) ** 2
     out = np.zeros(st.shape, dtype=np.result_type(E, kappa, float))
     for d in range(3):
         ax = _AXIS[d]
         D = face_D(st, E, kappa, d, freeze)
-        flux_p = D * (np.roll(E, -1, axis=ax) - E)      # through the +d face, into the cell
+        Enb = np.roll(E, -1, axis=ax)
+        if not st.periodic[d]:
+            last = [slice(None)] * 3
+            last[ax] = -1
+            Enb = Enb.copy()
+            Enb[tuple(last)] = 0.0                      # the ghost beyond the + boundary face
+        flux_p = D * (Enb - E)                          # through the +d face, into the cell
         flux_m = np.roll(flux_p, 1, axis=ax)            # the -d face is the -d neighbour's +d face
+        if not st.periodic[d]:
+            first = [slice(None)] * 3
+            first[ax] = slice(0, 1)
+            first = tuple(first)
+            flux_m = flux_m.copy()
+            # through the - boundary face, out of the cell into its ghost (E = 0)
+            flux_m[first] = lower_boundary_D(st, E, kappa, d, freeze) * (E[first] - 0.0)
         out = out + (flux_p - flux_m) / adx2
     return out
 

@@ -99,7 +99,7 @@ def _neighbourhood_step(w, run, c):
     srcs = np.asarray(w["src_index"])
     inside = np.isin(srcs, flat)
     local = np.array([np.nonzero(flat == q)[0][0] for q in srcs[inside]], np.int64)
-    sub.update(nx=3, ny=3, nz=3, periodic=(False, False, False), rho_b=w["rho_b"][sl], T0=w["T0"][sl],
+    sub.update(nx=3, ny=3, nz=3, periodic=(False, False, False), bc=None, rho_b=w["rho_b"][sl], T0=w["T0"][sl],
                v=tuple(v[sl] for v in w["v"]), clump=w["clump"][sl], E=run.E[sl], nHI=run.nHI[sl],
                src_index=local, src_ndot=np.asarray(w["src_ndot"])[inside])
     r = driver.Run(sub)

@@ -206,7 +206,7 @@ def test_face_limiter_matches_oracle(host_lib):
     host_lib.limiter_host(ctypes.c_int(n), *[_p(_arr(v)) for v in (Ei, Ej, ki, kj)], ctypes.c_double(adx),
                           ctypes.c_double(M.K.C_LIGHT), ctypes.c_double(E_min), _p(D), _p(Dt), _p(dD))
     st = SimpleNamespace(limiter="new", a=1.0, dx=adx, E_min=E_min, shape=(1, n, 2),
-                         periodic=(False, False, False), D_const=0.0)
+                         periodic=(False, False, False), faces=("reflect",) * 6, D_const=0.0)
 
     def oracle_D(ei):
         E = np.stack([ei, Ej + 0 * ei], axis=-1)[None]

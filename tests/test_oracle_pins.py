@@ -19,6 +19,7 @@ from oracle import diagnostics as D
 from oracle import driver
 from oracle import model as M
 from oracle import newton as N
+from oracle import newton as N_
 from oracle import rates
 from oracle import spectrum as S
 
@@ -237,6 +238,81 @@ def test_diffusion_conserves_energy_with_walls_and_periodic():
         nHI = 10 ** rng.uniform(-6, -3, st.shape)
         Ld = M.diffusion(st, E, M.opacity(st, nHI))
         assert abs(Ld.sum()) <= 1e-12 * np.abs(Ld).sum()
+
+
+def _image_extension(E, lower, upper):
+    """Periodic extension of a 1-D profile E (cells 0..N-1) whose rows 0..N-1 evolve like the
+    bounded problem: a reflecting face is a mirror plane for E (even image about the face), an
+    outflow face a node of an odd image about the ghost cell beyond it (which then holds 0)."""
+    N = len(E)
+    if (lower, upper) == ("reflect", "outflow"):          # even about face -1/2, odd about cell N
+        half = np.concatenate([E, [0.0], -E[::-1]])
+        return np.concatenate([half, half[::-1]])          # period 4N + 2
+    if (lower, upper) == ("outflow", "reflect"):
+        mirrored = _image_extension(E[::-1], "reflect", "outflow")[::-1]   # E in the last N cells
+        return np.roll(mirrored, N)
+    if (lower, upper) == ("outflow", "outflow"):          # odd about cell N and cell -1
+        return np.concatenate([E, [0.0], -E[::-1], [0.0]])
+    raise ValueError((lower, upper))
+
+
+@pytest.mark.parametrize("theta", [0.51, 1.0])
+@pytest.mark.parametrize("faces", [("reflect", "outflow"), ("outflow", "reflect"), ("outflow", "outflow")])
+def test_outflow_and_reflecting_faces_match_image_solutions(faces, theta):
+    """Constant-D diffusion on a bounded 1-D grid equals, row for row, the periodic problem whose
+    initial data are extended by images: an even image about a reflecting face and an odd image
+    about the ghost cell beyond an outflow face.  The periodic operator is itself pinned
+    (Fourier modes, Gaussian spreading); the images are exact for the discrete scheme because
+    it commutes with mirroring and with a change of sign.  A dropped ghost term, a ghost at the
+    wrong distance or a flipped sign breaks the agreement."""
+    N = 11
+    a, adot, dt, Dc, dx = 0.6, 1e-17, 4e13, 3e28, 3e21
+    rng = np.random.default_rng(17)
+    E1 = 1e-20 * (1.0 + rng.random(N))
+    bounded = _uniform_step((N, 1, 1), E_n=E1.reshape(1, 1, N).copy(), a=a, adot=adot, dt=dt, dx=dx,
+                            theta=theta, limiter="const", D_const=Dc, periodic=(False, False, False),
+                            bc=(faces[0], faces[1], "reflect", "reflect", "reflect", "reflect"))
+    Eext = _image_extension(E1, *faces)
+    L = len(Eext)
+    ext = _uniform_step((L, 1, 1), E_n=Eext.reshape(1, 1, L).copy(), a=a, adot=adot, dt=dt, dx=dx, theta=theta,
+                        limiter="const", D_const=Dc, periodic=(True, False, False))
+    for _ in range(2):
+        Ub, _ = N_.solve_step(bounded, tol=1e-12)
+        Ue, _ = N_.solve_step(ext, tol=1e-12)
+        np.testing.assert_allclose(Ub[2].ravel(), Ue[2].ravel()[:N], rtol=1e-11, atol=1e-13 * E1.max())
+        bounded.E_n, ext.E_n = Ub[2], Ue[2]
+    # and the bounded run really lost energy through its outflow face(s)
+    assert bounded.E_n.sum() < E1.sum() * (1 - 1e-3)
+
+
+def test_outflow_faces_lose_the_discrete_boundary_flux():
+    """Summed over the cells, the FLD operator with outflow faces equals minus the flux through
+    those faces alone (interior face fluxes cancel in pairs; reflecting faces carry none).  The
+    flux through an outflow face is D (E_i - 0) / (a dx)^2 per unit cell volume with D from
+    Eq. limiter between the cell and its empty ghost: face energy E_i / 2, hence R = 2 / (a dx),
+    and kappa_T the cell's own opacity.  With no opacity the face carries the free-streaming
+    limit of the limiter, c times the face energy: c E_i / 2."""
+    rng = np.random.default_rng(5)
+    shape = (3, 4, 5)
+    bc = ("outflow", "outflow", "reflect", "outflow", "outflow", "reflect")
+    for sigma in (6.3e-18, 0.0):
+        st = _uniform_step((5, 4, 3), periodic=(False, False, False), bc=bc, sigma_E=sigma, a=0.7,
+                           limiter="new")
+        E = 10 ** rng.uniform(-22, -16, shape)
+        nHI = 10 ** rng.uniform(-5, -2, shape)
+        kap = M.opacity(st, nHI)
+        adx = st.a * st.dx
+        total = M.diffusion(st, E, kap).sum()
+        loss = 0.0
+        for (ax, side) in ((2, 0), (2, -1), (1, -1), (0, 0)):      # the outflow faces
+            sl = [slice(None)] * 3
+            sl[ax] = side
+            Eb, kb = E[tuple(sl)], kap[tuple(sl)]
+            D = M.limiter_D(kb, 2.0 / adx)
+            if sigma == 0.0:
+                np.testing.assert_allclose(D * Eb / adx, K.C_LIGHT * Eb / 2, rtol=1e-14)
+            loss += np.sum(D * Eb) / adx**2
+        assert total == pytest.approx(-loss, rel=1e-12)
 
 
 @pytest.mark.parametrize("n,src", [((4, 3, 3), 4e-31), ((4, 3, 3), 0.0), ((1, 1, 5), 4e-31), ((2, 2, 2), 0.0),

@@ -18,7 +18,8 @@ conditions, which are not available):
 * ``stromgren_static``   -- isothermal Stromgren sphere in a static universe:
   uniform n_H = 1e-3 cm^-3 in a 6.6 kpc box, x_HI = 0.9999, T = 1e4 K,
   E = 1e-35 erg/cm^3, one corner source of 5e48 photons/s (one octant of it is
-  inside the box: zero-flux walls, Ndot/8 emitted into the octant).
+  inside the box: reflecting lower faces, Ndot/8 emitted into the octant; outflow at the
+  upper faces, as in the paper's verification problem).
 * ``stromgren_cosmo``    -- the same source in a comoving box of 400 kpc at the
   mean baryon density of flat LCDM (Omega_m 0.3, Omega_b 0.04, h 0.7), z = 10.
 * ``reionization_field`` -- periodic 14.4 Mpc comoving box at z = 9: log-normal
@@ -32,7 +33,8 @@ conditions, which are not available):
   section (Table 1: q0 in {0.5, 0.05}, z0 in {4, 10}, box L0 proper at z0, H0, Omega_b):
   uniform gas at Omega_b rho_crit (1+z0)^3 (the quoted rho_b0 for z0 = 4), fully neutral,
   T = 1e4 K (isothermal), E = 1e-35 erg/cm^3, one monochromatic 13.6 eV corner source of
-  5e48 photons/s (octant, zero-flux walls), case-B alpha = 2.59e-13, run from z0 to z = 0
+  5e48 photons/s (octant, reflecting lower and outflow upper faces), case-B alpha = 2.59e-13,
+  run from z0 to z = 0
   in steps evenly spaced in log t.
 * ``random_state``       -- random but physical states on small grids, for
   element-wise parity of single kernels.
@@ -53,15 +55,27 @@ LCDM = dict(Omega_m=0.3, Omega_L=0.7, Omega_b=0.04, h=0.7)
 RHO_CRIT_H2 = 1.8784723e-29    # g/cm^3 per h^2 (critical density today)
 
 
-def _base(n, L, periodic):
+# boundaries of the verification problems: reflecting at the lower faces, outflow at the upper
+# faces, per face in the order (x-, x+, y-, y+, z-, z+)
+PAPER_BC = ("reflect", "outflow") * 3
+
+
+def _base(n, L, periodic, bc=None):
+    """Grid shape, cell width and boundaries; bc (six face types) overrides periodic, whose axes
+    otherwise reflect at both faces."""
     nx, ny, nz = (n, n, n) if np.isscalar(n) else n
-    return dict(nx=int(nx), ny=int(ny), nz=int(nz), dx=float(L) / nx, periodic=tuple(periodic))
+    if bc is None:
+        bc = tuple(t for p in periodic for t in (("periodic",) * 2 if p else ("reflect",) * 2))
+    bc = tuple(bc)
+    periodic = tuple(bc[2 * d] == "periodic" for d in range(3))
+    return dict(nx=int(nx), ny=int(ny), nz=int(nz), dx=float(L) / nx, periodic=periodic, bc=bc)
 
 
 def stromgren_static(n=16, dt_over_trec=1e-2, nsteps=20, spectrum="blackbody", nH=1e-3,
-                     box_kpc=6.6, ndot=5e48, theta=1.0):
-    """Static-universe Stromgren sphere (octant with zero-flux walls, source in cell 0)."""
-    w = _base(n, box_kpc * KPC, (False, False, False))
+                     box_kpc=6.6, ndot=5e48, theta=1.0, bc=PAPER_BC):
+    """Static-universe Stromgren sphere (octant: reflecting lower faces, outflow upper faces,
+    source in cell 0)."""
+    w = _base(n, box_kpc * KPC, (False, False, False), bc)
     shape = (w["nz"], w["ny"], w["nx"])
     t_rec = 1.0 / (ALPHA_B_PAPER * nH)
     w.update(
@@ -81,9 +95,10 @@ def stromgren_static(n=16, dt_over_trec=1e-2, nsteps=20, spectrum="blackbody", n
 
 
 def stromgren_cosmo(n=128, z0=10.0, z_end=4.0, nsteps=500, box_kpc_comoving=400.0, ndot=5e48,
-                    spectrum="blackbody", theta=1.0):
-    """Cosmological Stromgren sphere in flat LCDM; the driver advances a(t) from z0."""
-    w = _base(n, box_kpc_comoving * KPC, (False, False, False))
+                    spectrum="blackbody", theta=1.0, bc=PAPER_BC):
+    """Cosmological Stromgren sphere in flat LCDM (octant, boundaries as stromgren_static); the
+    driver advances a(t) from z0."""
+    w = _base(n, box_kpc_comoving * KPC, (False, False, False), bc)
     shape = (w["nz"], w["ny"], w["nx"])
     nH = LCDM["Omega_b"] * RHO_CRIT_H2 * LCDM["h"] ** 2 / M_H
     w.update(
@@ -110,10 +125,10 @@ SG_TABLE1 = ((0.5, 4.0, 80.0, 0.5, 1.0, 0.0, 0.2),
              (0.05, 10.0, 27.0, 1.0, 0.1, 0.0, 0.1))
 
 
-def shapiro_giroux(row, n=32, nsteps=200, ndot=5e48, theta=1.0):
+def shapiro_giroux(row, n=32, nsteps=200, ndot=5e48, theta=1.0, bc=PAPER_BC):
     """Row ``row`` of Table 1 (see the module docstring); comoving box L0 (1 + z0)."""
     q0, z0, L0, h, Om, OL, Ob = SG_TABLE1[row]
-    w = _base(n, L0 * KPC * (1.0 + z0), (False, False, False))
+    w = _base(n, L0 * KPC * (1.0 + z0), (False, False, False), bc)
     shape = (w["nz"], w["ny"], w["nx"])
     nH = Ob * RHO_CRIT_H2 * h**2 / M_H            # comoving (proper at z0: times (1 + z0)^3)
     w.update(
@@ -208,7 +223,7 @@ def reionization_field(n=256, nsrc=2000, seed=9001, box_mpc=14.4, z0=9.0, dt_myr
 
 
 def random_state(shape, seed=0, periodic=(True, True, True), isothermal=True, nsrc=3, box_kpc=100.0,
-                 theta=0.51, dt_myr=None):
+                 theta=0.51, dt_myr=None, bc=None):
     """A random physical state for element-wise kernel parity.
 
     Densities n_H in [1e-4, 1e-2] cm^-3, neutral fractions log-uniform in [1e-6, 1),
@@ -217,7 +232,7 @@ def random_state(shape, seed=0, periodic=(True, True, True), isothermal=True, ns
     """
     rng = np.random.default_rng(seed)
     nz, ny, nx = shape
-    w = _base((nx, ny, nz), box_kpc * KPC, periodic)
+    w = _base((nx, ny, nz), box_kpc * KPC, periodic, bc)
     nH = 10 ** rng.uniform(-4, -2, shape)
     xHI = 10 ** rng.uniform(-6, -1e-6, shape)
     E = 10 ** rng.uniform(-30, -12, shape)
