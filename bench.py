@@ -467,13 +467,30 @@ def bench_line(args, res, world, peaks):
     launches = sum(x["kernel_launches"] for x in res["stats"]) + len(res["stats"])
     w_desc = (f"reionization-like field {args.size}^3, {workload_sources(args.size)} sources, z=9, dt=1 Myr, "
               "theta=1")
+    config = {"workload": w_desc, "grid": args.size, "precision": "mixed (FP32 multigrid in FP64 Newton/CG)",
+              "newton_tol": args.newton_tol, "lin_rtol": args.lin_rtol, "parallelism": f"replicas x{world}",
+              "l2": l2_note(args.size)}
+    fp64 = res["fp64"]
+    if fp64:
+        # the all-FP64 arm and the mixed-vs-FP64 comparison, kept in the config block
+        config["fp64_path"] = {"value": fp64["value"], "ms_per_step": fp64["ms_per_step"],
+                               "speedup_mixed_vs_fp64": fp64["speedup_mixed_vs_fp64"],
+                               "newton_iters": fp64["newton_iters"], "linear_iters": fp64["linear_iters"]}
+        config["mixed_vs_fp64_error"] = fp64["mixed_vs_fp64_error"]
+    config["mixed_iters"] = {"newton_iters": [x["newton_iters"] for x in res["stats"]],
+                             "linear_iters": [x["linear_iters"] for x in res["stats"]]}
+    # per kernel class: share of the step and achieved GB/s on its algorithmic bytes
+    config["kernel_shares"] = {k: [round(v["share"], 4), round(v["GBps"], 1) if v["GBps"] else None]
+                               for k, v in kernels.items()}
+    if roof_mg is not None:
+        config["vcycle_smoother"] = {k: roof_mg[k] for k in ("achieved", "frac", "share_of_step")}
+        if "fine_level" in roof_mg:
+            config["vcycle_smoother"]["fine_level"] = roof_mg["fine_level"]
     line = {
         "metric": METRIC, "value": res["value"], "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-        "config": {"workload": w_desc, "grid": args.size, "precision": "mixed (FP32 multigrid in FP64 Newton/CG)",
-                   "newton_tol": args.newton_tol, "lin_rtol": args.lin_rtol, "parallelism": f"replicas x{world}",
-                   "l2": l2_note(args.size)},
+        "config": config,
         "newton_iters": [x["newton_iters"] for x in res["stats"]],
         "linear_iters": [x["linear_iters"] for x in res["stats"]],
         "fp64": res["fp64"],

@@ -50,7 +50,12 @@ extern "C" {
 #define RT_ENONFINITE 6    /* a residual or linear-solver quantity became NaN/Inf    */
 #define RT_ELINEAR 7       /* the linear solver did not reach lin_rtol in max_lin    */
 
-enum { RT_BC_PERIODIC = 0, RT_BC_WALL = 1 };            /* per axis; WALL = zero flux   */
+/* Boundary type of a face (Sec. "Verification tests": reflecting at the lower faces, outflow at
+ * the upper faces).  PERIODIC must be set on both faces of an axis.  REFLECT (alias WALL): no
+ * flux through the face.  OUTFLOW: radiation leaves freely -- the cell beyond the face is an empty
+ * ghost (E = 0) holding a copy of the boundary cell's gas, and the face's flux-limited diffusion
+ * coefficient follows Eq. limiter between the two (free-streaming limit: c E / 2 per unit area). */
+enum { RT_BC_PERIODIC = 0, RT_BC_REFLECT = 1, RT_BC_WALL = 1, RT_BC_OUTFLOW = 2 };
 enum { RT_FP64 = 0, RT_MIXED = 1 };                     /* multigrid precision          */
 enum { RT_SPECTRUM_MONO = 0, RT_SPECTRUM_BLACKBODY = 1 };
 enum { RT_RECOMB_CONST = 0, RT_RECOMB_HG97 = 1 };
@@ -63,7 +68,8 @@ typedef struct {
                              FP32 / 2048 FP64); a level above that bound with an odd dim is
                              rejected with RT_EINVAL                                         */
     double dx;            /* comoving cell width, normalised (cm / u_x)                     */
-    int bc[3];            /* boundary per axis (x, y, z): RT_BC_PERIODIC or RT_BC_WALL        */
+    int bc[6];            /* boundary per face (x-, x+, y-, y+, z-, z+): RT_BC_PERIODIC on both
+                             faces of an axis, else RT_BC_REFLECT or RT_BC_OUTFLOW per face   */
     double u_x, u_t, u_g; /* unit factors of Eq. units: cm, s, g                               */
     double theta;         /* two-level time parameter of Eq. radiation_residual (paper: 0.51) */
     int precision;        /* RT_FP64 or RT_MIXED (FP32 multigrid inside FP64 Newton/CG)       */

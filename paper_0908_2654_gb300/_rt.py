@@ -15,7 +15,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "librtfld.so")
 
 RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOCONV, RT_ELINESEARCH, RT_ENONFINITE, RT_ELINEAR = range(8)
-RT_BC_PERIODIC, RT_BC_WALL = 0, 1
+RT_BC_PERIODIC, RT_BC_REFLECT, RT_BC_OUTFLOW = 0, 1, 2
+RT_BC_WALL = RT_BC_REFLECT
 RT_FP64, RT_MIXED = 0, 1
 RT_SPECTRUM_MONO, RT_SPECTRUM_BLACKBODY = 0, 1
 RT_RECOMB_CONST, RT_RECOMB_HG97 = 0, 1
@@ -28,7 +29,7 @@ class GridDesc(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
         ("dx", ctypes.c_double),
-        ("bc", ctypes.c_int * 3),
+        ("bc", ctypes.c_int * 6),
         ("u_x", ctypes.c_double), ("u_t", ctypes.c_double), ("u_g", ctypes.c_double),
         ("theta", ctypes.c_double),
         ("precision", ctypes.c_int),

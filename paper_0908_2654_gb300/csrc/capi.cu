@@ -158,11 +158,11 @@ struct rt_grid {
     double *Xec, *Xnc, *Xet, *Xnt;   // local-elimination sensitivities (current / trial)
     double *He10, *He20, *He1c, *He2c, *He1t, *He2t;   // helium: start, current, trial (n_HeI, n_HeII)
     // CG vectors
-    double *x, *r, *z, *p, *q;
+    double *x, *r, *z, *z2, *p, *q;   // z2: second buffer of the FP64 V-cycle's level 0
     // multigrid
     Hierarchy<float> mgf;
     Hierarchy<double> mgd;
-    float *bf, *xf;           // FP32 level-0 right side / solution (mixed)
+    float *bf, *xf, *xf2;     // FP32 level-0 right side / solution and its second buffer (mixed)
     // reductions
     double *partials, *dots, *scal;
     int* d_err;
@@ -201,13 +201,13 @@ int check_launch(const char* what) {
 
 enum KClass {
     K_ZERO, K_SOURCES, K_FACES, K_SETUP, K_ASSEMBLE, K_FINALIZE, K_SPMV, K_RESNORM, K_CG_UPDATE, K_DOT2, K_P_UPDATE,
-    K_SCALARS, K_COPY, K_CAST, K_MG_DIAG, K_COARSEN, K_RBGS, K_RESTRICT, K_PROLONG, K_TAIL, K_ADD, K_ADVECT,
+    K_SCALARS, K_COPY, K_CAST, K_MG_DIAG, K_COARSEN, K_RBGS, K_RESTRICT, K_TAIL, K_ADD, K_ADVECT,
     K_ADVECT_CHECK, K_RBGS_FINE, K_NCLASS
 };
 const char* kClassName[K_NCLASS] = {"zero", "scatter_sources", "faces", "setup", "newton_assemble", "finalize",
                                     "cg_spmv_dot", "cg_residual", "cg_update_xr", "cg_dot2", "cg_p_update",
                                     "cg_scalars", "copy", "cast", "mg_diag", "mg_coarsen", "mg_rbgs",
-                                    "mg_resid_restrict", "mg_prolong_add", "mg_coarse_cta", "add", "advect",
+                                    "mg_resid_restrict", "mg_coarse_cta", "add", "advect",
                                     "advect_courant", "mg_rbgs_fine"};
 
 // Launch f() as kernel class cls moving `bytes` algorithmic bytes; brackets it with events
@@ -261,6 +261,7 @@ HierarchyStatus build_hierarchy(rt_grid* g, Hierarchy<T>& H, T* diag0, T* wx0, T
     L.wy = wy0;
     L.wz = wz0;
     L.x = nullptr;   // level 0 vectors are bound per solve
+    L.xt = nullptr;
     L.b = nullptr;
     H.lv.push_back(L);
     while (d.n() > TailMax<T>::value) {
@@ -276,8 +277,10 @@ HierarchyStatus build_hierarchy(rt_grid* g, Hierarchy<T>& H, T* diag0, T* wx0, T
         c.wy = dalloc<T>(n, ok);
         c.wz = dalloc<T>(n, ok);
         c.x = dalloc<T>(n, ok);
+        c.xt = dalloc<T>(n, ok);
         c.b = dalloc<T>(n, ok);
-        for (void* p : {(void*)c.diag, (void*)c.wx, (void*)c.wy, (void*)c.wz, (void*)c.x, (void*)c.b}) H.owned.push_back(p);
+        for (void* p : {(void*)c.diag, (void*)c.wx, (void*)c.wy, (void*)c.wz, (void*)c.x, (void*)c.xt, (void*)c.b})
+            H.owned.push_back(p);
         if (!ok) return HIER_NOMEM;
         H.lv.push_back(c);
     }
@@ -299,39 +302,47 @@ void mg_setup(rt_grid* g, Hierarchy<T>& H) {
     }
 }
 
-// one V-cycle on the hierarchy: level-0 b and x must be bound
+// nu red-black Gauss-Seidel sweeps on level L (first colour `first`), each from L.x into L.xt
+// and then swapped; the first sweep starts from a zero iterate (zero) or from L.x plus the
+// prolongated correction of `coarse`
+template <class T>
+void smooth(rt_grid* g, Level<T>& L, int nu, int first, bool zero, const Level<T>* coarse, int cls) {
+    const double n = (double)L.d.n(), t = sizeof(T);
+    for (int k = 0; k < nu; ++k) {
+        const bool z0 = zero && k == 0;
+        const Level<T>* c = k == 0 ? coarse : nullptr;
+        // algorithmic words per cell of a sweep: b, diag, wx, wy, wz and the old iterate read once,
+        // the new iterate written once (no old iterate from zero; the coarse correction adds the
+        // coarse level's x, 1/8 word per fine cell)
+        const double words = (z0 ? 6.0 : 7.0) + (c ? 0.125 : 0.0);
+        run(g, cls, n * words * t, [&] { launch_rbgs_sweep<T>(L, first, z0, c, g->stream); });
+        std::swap(L.x, L.xt);
+    }
+}
+
+// one V-cycle on the hierarchy: level-0 b, x and xt must be bound; the result is left in
+// level 0's x (which may be either of the two level-0 buffers)
 template <class T>
 void vcycle(rt_grid* g, Hierarchy<T>& H) {
     const int nu1 = g->desc.mg_nu1, nu2 = g->desc.mg_nu2;
     const int last = (int)H.lv.size() - 1;
     cudaStream_t s = g->stream;
     const double t = sizeof(T);
-    // algorithmic bytes per cell of one colour pass: own b and diag, all face couplings
-    // (own + faces and neighbours' + faces = own - faces), all x read, own x written
-    const double rb = 5.5 * t;
     for (int l = 0; l < last; ++l) {
         const double n = (double)H.lv[l].d.n();
         const int cls = l == 0 ? K_RBGS_FINE : K_RBGS;   // the fine level timed on its own
-        for (int k = 0; k < nu1; ++k) {
-            run(g, cls, n * rb, [&] { launch_rbgs<T>(H.lv[l], 0, k == 0, s); });
-            run(g, cls, n * rb, [&] { launch_rbgs<T>(H.lv[l], 1, false, s); });
-        }
+        smooth<T>(g, H.lv[l], nu1, 0, true, nullptr, cls);
         run(g, K_RESTRICT, n * 6.125 * t, [&] { launch_resid_restrict<T>(H.lv[l], H.lv[l + 1], s); });
     }
     run(g, K_TAIL, (double)H.lv[last].d.n() * 6 * t, [&] { launch_tail<T>(H.lv[last], 1, std::max(nu1, 1), s); });
     for (int l = last - 1; l >= 0; --l) {
-        const double n = (double)H.lv[l].d.n();
-        run(g, K_PROLONG, n * 2.125 * t, [&] { launch_prolong_add<T>(H.lv[l + 1], H.lv[l], s); });
         const int cls = l == 0 ? K_RBGS_FINE : K_RBGS;
-        for (int k = 0; k < nu2; ++k) {
-            run(g, cls, n * rb, [&] { launch_rbgs<T>(H.lv[l], 1, false, s); });
-            run(g, cls, n * rb, [&] { launch_rbgs<T>(H.lv[l], 0, false, s); });
-        }
+        smooth<T>(g, H.lv[l], nu2, 1, false, &H.lv[l + 1], cls);
     }
 }
 
-// z = M^{-1} r
-void precondition(rt_grid* g, const double* r, double* z) {
+// z = M^{-1} r into g->z
+void precondition(rt_grid* g, const double* r) {
     cudaStream_t s = g->stream;
     const double n = (double)g->n;
     if (g->desc.precision == RT_MIXED) {
@@ -339,14 +350,20 @@ void precondition(rt_grid* g, const double* r, double* z) {
         // update) so that the FP32 copy neither overflows nor underflows; z is scaled back
         const double* amax = g->dots + 1;
         run(g, K_CAST, n * 12, [&] { launch_cast_d2f_scaled(g->n, r, g->bf, amax, s); });
-        g->mgf.lv[0].b = g->bf;
-        g->mgf.lv[0].x = g->xf;
+        Level<float>& L0 = g->mgf.lv[0];
+        L0.b = g->bf;
+        L0.x = g->xf;
+        L0.xt = g->xf2;
         vcycle<float>(g, g->mgf);
-        run(g, K_CAST, n * 12, [&] { launch_cast_f2d_scaled(g->n, g->xf, z, amax, s); });
+        const float* xr = L0.x;
+        run(g, K_CAST, n * 12, [&] { launch_cast_f2d_scaled(g->n, xr, g->z, amax, s); });
     } else {
-        g->mgd.lv[0].b = const_cast<double*>(r);
-        g->mgd.lv[0].x = z;
+        Level<double>& L0 = g->mgd.lv[0];
+        L0.b = const_cast<double*>(r);
+        L0.x = g->z;
+        L0.xt = g->z2;
         vcycle<double>(g, g->mgd);
+        if (L0.x != g->z) std::swap(g->z, g->z2);   // the result is in the other buffer
     }
 }
 
@@ -379,7 +396,7 @@ int pcg(rt_grid* g, const double* b, double* x, const double* w, double rtol, in
         return RT_ENONFINITE;
     }
     if (rn0 == 0.0) return RT_OK;
-    precondition(g, g->r, g->z);
+    precondition(g, g->r);
     run(g, K_DOT2, N * 16, [&] { nb = launch_dot2(n, g->z, g->r, nullptr, g->partials, s); });
     run(g, K_FINALIZE, 0.0, [&] { launch_finalize(g->partials, nb, 2, g->dots, s); });
     run(g, K_SCALARS, 0.0, [&] { launch_cg_scalars(g->scal, g->dots, 0, s); });
@@ -403,7 +420,7 @@ int pcg(rt_grid* g, const double* b, double* x, const double* w, double rtol, in
         }
         if (rn <= rtol * rn0) return RT_OK;
         if (k == maxit) break;
-        precondition(g, g->r, g->z);
+        precondition(g, g->r);
         run(g, K_DOT2, N * 24, [&] { nb = launch_dot2(n, g->z, g->r, g->q, g->partials, s); });
         run(g, K_FINALIZE, 0.0, [&] { launch_finalize(g->partials, nb, 2, g->dots, s); });
         run(g, K_SCALARS, 0.0, [&] { launch_cg_scalars(g->scal, g->dots, 2, s); });
@@ -448,19 +465,101 @@ int validate_inputs(const rt_grid* g, const rt_step_inputs* in) {
     return RT_OK;
 }
 
-PhysParams step_params(const rt_grid* g, const rt_step_inputs* in) {
-    PhysParams P = g->base;
+// per-step values of PhysParams: expansion, step length, face-coupling scale
+void apply_step(PhysParams& P, const rt_grid_desc& d, const rt_step_inputs* in) {
     P.a = in->a;
     P.a3 = in->a * in->a * in->a;
     P.H = in->adot / in->a;
     P.dt = in->dt;
-    P.adx = in->a * g->desc.dx;
-    P.wscale = in->dt * g->desc.theta / (P.adx * P.adx);
+    P.adx = in->a * d.dx;
+    P.wscale = in->dt * d.theta / (P.adx * P.adx);
     const double x = 2.0 * P.H * in->dt;
     P.phi_e = in->dt * (std::fabs(x) < 1e-8 ? 1.0 - 0.5 * x + x * x / 6.0 : -std::expm1(-x) / x);
     // the local equations are solved three orders of magnitude below the Newton tolerance
-    P.local_tol = std::max(1e-14, 1e-3 * g->desc.newton_tol);
+    P.local_tol = std::max(1e-14, 1e-3 * d.newton_tol);
+}
+
+PhysParams step_params(const rt_grid* g, const rt_step_inputs* in) {
+    PhysParams P = g->base;
+    apply_step(P, g->desc, in);
     return P;
+}
+
+// Checks of the descriptor's geometry, units, theta and boundaries (every entry point that
+// takes a descriptor); sets the detail text and returns RT_EINVAL on the first failure.
+int check_geometry(const rt_grid_desc& d) {
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1 || !(d.dx > 0) || !(d.u_x > 0) || !(d.u_t > 0) || !(d.u_g > 0)) {
+        set_detail("grid dims, dx and unit factors must be positive");
+        return RT_EINVAL;
+    }
+    if (!(d.theta > 0.0 && d.theta <= 1.0)) {
+        set_detail("theta must lie in (0, 1]");
+        return RT_EINVAL;
+    }
+    for (int f = 0; f < 6; ++f)
+        if (d.bc[f] != RT_BC_PERIODIC && d.bc[f] != RT_BC_REFLECT && d.bc[f] != RT_BC_OUTFLOW) {
+            set_detail("unknown boundary type on face %d", f);
+            return RT_EINVAL;
+        }
+    for (int k = 0; k < 3; ++k)
+        if ((d.bc[2 * k] == RT_BC_PERIODIC) != (d.bc[2 * k + 1] == RT_BC_PERIODIC)) {
+            set_detail("axis %d: periodic on one face only", k);
+            return RT_EINVAL;
+        }
+    return RT_OK;
+}
+
+// Step-independent PhysParams of a descriptor: unit factors (Eqs. units, scalings), the grey
+// constants of Eq. grey_definition in normalised units, boundaries and physics switches.
+PhysParams base_params(const rt_grid_desc& d, const Grey& grey) {
+    const double u_d = d.u_g / (d.u_x * d.u_x * d.u_x), u_v = d.u_x / d.u_t;
+    const double u_E = u_d * u_v * u_v, u_n = u_d / kMH;
+    PhysParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.nx = d.nx;
+    P.ny = d.ny;
+    P.nz = d.nz;
+    for (int k = 0; k < 3; ++k) P.per[k] = d.bc[2 * k] == RT_BC_PERIODIC;
+    for (int f = 0; f < 6; ++f) P.outflow[f] = d.bc[f] == RT_BC_OUTFLOW;
+    P.dx = d.dx;
+    P.theta = d.theta;
+    P.c = kC * d.u_t / d.u_x;
+    P.kE = grey.sigma_E * u_n * d.u_x;
+    P.kG = kC * grey.sigma_G * u_E * d.u_t;
+    P.kA = d.u_t * u_n;
+    P.kH = kC * u_n * (grey.sigma_E - kHnu0 * grey.sigma_G) * d.u_t;
+    P.kC = d.u_t / u_E;
+    P.kT = (kGamma - 1.0) * u_v * u_v * kMH / kKB;
+    P.un = u_n;
+    P.E_min = (d.E_min > 0 ? d.E_min : 1e-35) / u_E;
+    P.E_floor = P.E_min;
+    P.e_floor = kKB * 1.0 / ((kGamma - 1.0) * kMH) / (u_v * u_v);
+    P.T_iso = d.T_iso;
+    P.D_const = d.D_const * d.u_t / (d.u_x * d.u_x);
+    P.src_scale = grey.eps_src * d.u_t / (d.u_x * d.u_x * d.u_x * u_E * d.dx * d.dx * d.dx);
+    P.alpha_const = kAlphaB;
+    P.isothermal = d.isothermal;
+    P.helium = d.helium;
+    P.Y = d.helium ? d.Y : 0.0;
+    if (d.helium) {
+        const GreyHe h = helium_grey_constants(d.spectrum, d.T_B);
+        P.kE1 = h.sE1 * u_n * d.u_x;
+        P.kE2 = h.sE2 * u_n * d.u_x;
+        P.kG1 = kC * h.sG1 * u_E * d.u_t;
+        P.kG2 = kC * h.sG2 * u_E * d.u_t;
+        P.kH1 = kC * u_n * (h.sE1 - kHnuHeI * h.sG1) * d.u_t;
+        P.kH2 = kC * u_n * (h.sE2 - kHnuHeII * h.sG2) * d.u_t;
+    }
+    P.recomb = d.recomb;
+    P.cooling = d.cooling;
+    P.limiter = d.limiter;
+    return P;
+}
+
+bool has_outflow(const rt_grid_desc& d) {
+    for (int f = 0; f < 6; ++f)
+        if (d.bc[f] == RT_BC_OUTFLOW) return true;
+    return false;
 }
 
 // sources, faces, explicit part, initial iterate into (Ec, nc, ecc); sets P.E_floor
@@ -563,13 +662,17 @@ int advect_call(rt_grid* g, const rt_step_inputs* in, const rt_state* src, rt_st
         set_detail("invalid expansion factor or time step (a = %g, dt = %g)", in->a, in->dt);
         return RT_EINVAL;
     }
+    if (has_outflow(g->desc)) {
+        set_detail("the advection pre-step covers periodic and reflecting faces");
+        return RT_EINVAL;
+    }
     RT_CUDA(cudaSetDevice(g->desc.device));
     AdvectArgs A;
     std::memset(&A, 0, sizeof(A));
     A.nx = g->desc.nx;
     A.ny = g->desc.ny;
     A.nz = g->desc.nz;
-    for (int d = 0; d < 3; ++d) A.per[d] = g->desc.bc[d] == RT_BC_PERIODIC;
+    for (int d = 0; d < 3; ++d) A.per[d] = g->desc.bc[2 * d] == RT_BC_PERIODIC;
     A.k = in->dt / (in->a * g->desc.dx);
     A.v[0] = in->vx;
     A.v[1] = in->vy;
@@ -639,7 +742,7 @@ void rt_destroy_grid(rt_grid* g) {
     if (!g) return;
     cudaSetDevice(g->desc.device);
     double* bufs[] = {g->E0, g->n0, g->src, g->bE, g->wx, g->wy, g->wz, g->Ec, g->nc, g->ecc, g->Et, g->nt, g->ect,
-                      g->step, g->diag, g->rhs, g->wE, g->x, g->r, g->z, g->p, g->q, g->partials, g->dots, g->scal,
+                      g->step, g->diag, g->rhs, g->wE, g->x, g->r, g->z, g->z2, g->p, g->q, g->partials, g->dots, g->scal,
                       g->Xec, g->Xnc, g->Xet, g->Xnt, g->He10, g->He20, g->He1c, g->He2c, g->He1t, g->He2t};
     for (double* b : bufs) cudaFree(b);
     cudaFree(g->wxf);
@@ -647,6 +750,7 @@ void rt_destroy_grid(rt_grid* g) {
     cudaFree(g->wzf);
     cudaFree(g->bf);
     cudaFree(g->xf);
+    cudaFree(g->xf2);
     cudaFree(g->d_err);
     if (g->mgf.lv.size() > 0) cudaFree(g->mgf.lv[0].diag);
     if (g->mgd.lv.size() > 0) cudaFree(g->mgd.lv[0].diag);
@@ -664,19 +768,7 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out) {
     }
     *out = nullptr;
     const rt_grid_desc& d = *desc;
-    if (d.nx < 1 || d.ny < 1 || d.nz < 1 || !(d.dx > 0) || !(d.u_x > 0) || !(d.u_t > 0) || !(d.u_g > 0)) {
-        set_detail("grid dims, dx and unit factors must be positive");
-        return RT_EINVAL;
-    }
-    if (!(d.theta > 0.0 && d.theta <= 1.0)) {
-        set_detail("theta must lie in (0, 1]");
-        return RT_EINVAL;
-    }
-    for (int k = 0; k < 3; ++k)
-        if (d.bc[k] != RT_BC_PERIODIC && d.bc[k] != RT_BC_WALL) {
-            set_detail("unknown boundary type on axis %d", k);
-            return RT_EINVAL;
-        }
+    if (check_geometry(d)) return RT_EINVAL;
     if ((d.precision != RT_FP64 && d.precision != RT_MIXED) || d.mg_nu1 < 1 || d.mg_nu2 < 1 || d.max_newton < 1 ||
         d.max_lin < 1 || !(d.newton_tol > 0) || !(d.lin_rtol > 0) || (d.helium != 0 && d.helium != 1) ||
         (d.helium && !(d.Y >= 0.0 && d.Y < 1.0))) {
@@ -704,7 +796,7 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out) {
     g->dims.nx = d.nx;
     g->dims.ny = d.ny;
     g->dims.nz = d.nz;
-    for (int k = 0; k < 3; ++k) g->dims.per[k] = d.bc[k] == RT_BC_PERIODIC;
+    for (int k = 0; k < 3; ++k) g->dims.per[k] = d.bc[2 * k] == RT_BC_PERIODIC;
     g->n = g->dims.n();
     g->grey = grey_constants(d.spectrum, d.T_B);
 
@@ -716,43 +808,7 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out) {
     g->u_v = d.u_x / d.u_t;
     g->u_E = g->u_d * g->u_v * g->u_v;
     g->u_n = g->u_d / kMH;
-    PhysParams& P = g->base;
-    std::memset(&P, 0, sizeof(P));
-    P.nx = d.nx;
-    P.ny = d.ny;
-    P.nz = d.nz;
-    for (int k = 0; k < 3; ++k) P.per[k] = g->dims.per[k];
-    P.dx = d.dx;
-    P.theta = d.theta;
-    P.c = kC * d.u_t / d.u_x;
-    P.kE = g->grey.sigma_E * g->u_n * d.u_x;
-    P.kG = kC * g->grey.sigma_G * g->u_E * d.u_t;
-    P.kA = d.u_t * g->u_n;
-    P.kH = kC * g->u_n * (g->grey.sigma_E - kHnu0 * g->grey.sigma_G) * d.u_t;
-    P.kC = d.u_t / g->u_E;
-    P.kT = (kGamma - 1.0) * g->u_v * g->u_v * kMH / kKB;
-    P.un = g->u_n;
-    P.E_min = (d.E_min > 0 ? d.E_min : 1e-35) / g->u_E;
-    P.e_floor = kKB * 1.0 / ((kGamma - 1.0) * kMH) / (g->u_v * g->u_v);
-    P.T_iso = d.T_iso;
-    P.D_const = d.D_const * d.u_t / (d.u_x * d.u_x);
-    P.src_scale = g->grey.eps_src * d.u_t / (d.u_x * d.u_x * d.u_x * g->u_E * d.dx * d.dx * d.dx);
-    P.alpha_const = kAlphaB;
-    P.isothermal = d.isothermal;
-    P.helium = d.helium;
-    P.Y = d.helium ? d.Y : 0.0;
-    if (d.helium) {
-        const GreyHe h = helium_grey_constants(d.spectrum, d.T_B);
-        P.kE1 = h.sE1 * g->u_n * d.u_x;
-        P.kE2 = h.sE2 * g->u_n * d.u_x;
-        P.kG1 = kC * h.sG1 * g->u_E * d.u_t;
-        P.kG2 = kC * h.sG2 * g->u_E * d.u_t;
-        P.kH1 = kC * g->u_n * (h.sE1 - kHnuHeI * h.sG1) * d.u_t;
-        P.kH2 = kC * g->u_n * (h.sE2 - kHnuHeII * h.sG2) * d.u_t;
-    }
-    P.recomb = d.recomb;
-    P.cooling = d.cooling;
-    P.limiter = d.limiter;
+    g->base = base_params(d, g->grey);
 
     bool ok = true;
     const size_t n = (size_t)g->n;
@@ -780,6 +836,7 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out) {
         g->wzf = dalloc<float>(n, ok);
         g->bf = dalloc<float>(n, ok);
         g->xf = dalloc<float>(n, ok);
+        g->xf2 = dalloc<float>(n, ok);
         float* diag0 = dalloc<float>(n, ok);
         if (!ok) {
             cudaFree(diag0);
@@ -794,6 +851,7 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out) {
             if (hs == HIER_NOMEM) ok = false;
         }
     } else if (ok) {
+        g->z2 = dalloc<double>(n, ok);
         double* diag0 = dalloc<double>(n, ok);
         if (!ok) {
             cudaFree(diag0);
@@ -1210,6 +1268,10 @@ int rt_adjoint_step(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, c
         set_detail("the discrete adjoint covers hydrogen-only grids");
         return RT_EINVAL;
     }
+    if (g && has_outflow(g->desc)) {
+        set_detail("the discrete adjoint covers periodic and reflecting faces");
+        return RT_EINVAL;
+    }
     if (!g || !U_n || !U_np1 || !lam_np1 || !lam_n || !U_n->E || !U_n->n_HI || !U_np1->E || !U_np1->n_HI ||
         !U_np1->e_c || !lam_np1->E || !lam_np1->n_HI || !lam_np1->e_c || !lam_n->E || !lam_n->n_HI || !lam_n->e_c) {
         set_detail("null state or adjoint array");
@@ -1274,58 +1336,11 @@ int rt_adjoint_step(rt_grid* g, const rt_step_inputs* in, const rt_state* U_n, c
 // Used by the allocation-free entry point in noalloc.cu.
 int rt_internal_step_params(const rt_grid_desc* desc, const rt_step_inputs* in, PhysParams* out) {
     if (!desc || !in || !out) return RT_EINVAL;
-    const rt_grid_desc& d = *desc;
-    if (d.nx < 1 || d.ny < 1 || d.nz < 1 || !(d.dx > 0) || !(d.u_x > 0) || !(d.u_t > 0) || !(d.u_g > 0) ||
-        !(d.theta > 0.0 && d.theta <= 1.0)) {
-        set_detail("invalid descriptor");
-        return RT_EINVAL;
-    }
-    for (int k = 0; k < 3; ++k)
-        if (d.bc[k] != RT_BC_PERIODIC && d.bc[k] != RT_BC_WALL) {
-            set_detail("unknown boundary type on axis %d", k);
-            return RT_EINVAL;
-        }
+    if (check_geometry(*desc)) return RT_EINVAL;
     int rc = validate_inputs(nullptr, in);
     if (rc) return rc;
-    const Grey grey = grey_constants(d.spectrum, d.T_B);
-    const double u_d = d.u_g / (d.u_x * d.u_x * d.u_x), u_v = d.u_x / d.u_t;
-    const double u_E = u_d * u_v * u_v, u_n = u_d / kMH;
-    PhysParams P;
-    std::memset(&P, 0, sizeof(P));
-    P.nx = d.nx;
-    P.ny = d.ny;
-    P.nz = d.nz;
-    for (int k = 0; k < 3; ++k) P.per[k] = d.bc[k] == RT_BC_PERIODIC;
-    P.dx = d.dx;
-    P.theta = d.theta;
-    P.c = kC * d.u_t / d.u_x;
-    P.kE = grey.sigma_E * u_n * d.u_x;
-    P.kG = kC * grey.sigma_G * u_E * d.u_t;
-    P.kA = d.u_t * u_n;
-    P.kH = kC * u_n * (grey.sigma_E - kHnu0 * grey.sigma_G) * d.u_t;
-    P.kC = d.u_t / u_E;
-    P.kT = (kGamma - 1.0) * u_v * u_v * kMH / kKB;
-    P.un = u_n;
-    P.E_min = (d.E_min > 0 ? d.E_min : 1e-35) / u_E;
-    P.E_floor = P.E_min;
-    P.e_floor = kKB * 1.0 / ((kGamma - 1.0) * kMH) / (u_v * u_v);
-    P.T_iso = d.T_iso;
-    P.D_const = d.D_const * d.u_t / (d.u_x * d.u_x);
-    P.src_scale = grey.eps_src * d.u_t / (d.u_x * d.u_x * d.u_x * u_E * d.dx * d.dx * d.dx);
-    P.alpha_const = kAlphaB;
-    P.isothermal = d.isothermal;
-    P.recomb = d.recomb;
-    P.cooling = d.cooling;
-    P.limiter = d.limiter;
-    P.a = in->a;
-    P.a3 = in->a * in->a * in->a;
-    P.H = in->adot / in->a;
-    P.dt = in->dt;
-    P.adx = in->a * d.dx;
-    P.wscale = in->dt * d.theta / (P.adx * P.adx);
-    const double x = 2.0 * P.H * in->dt;
-    P.phi_e = in->dt * (std::fabs(x) < 1e-8 ? 1.0 - 0.5 * x + x * x / 6.0 : -std::expm1(-x) / x);
-    P.local_tol = std::max(1e-14, 1e-3 * d.newton_tol);
+    PhysParams P = base_params(*desc, grey_constants(desc->spectrum, desc->T_B));
+    apply_step(P, *desc, in);
     *out = P;
     return RT_OK;
 }

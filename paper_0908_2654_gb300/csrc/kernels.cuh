@@ -181,17 +181,18 @@ struct Level {
     T* wx;
     T* wy;
     T* wz;
-    T* x;
+    T* x;      // current iterate
+    T* xt;     // second iterate buffer: a sweep reads x and writes xt, then the two swap
     T* b;
 };
 template <class T>
 void launch_coarsen(const Level<T>& f, const Level<T>& c, cudaStream_t s);
+// one red-black Gauss-Seidel sweep (first colour `first`) from L.x into L.xt; from a zero iterate
+// (zero_guess) or from L.x plus the prolongation of coarse->x (coarse not null)
 template <class T>
-void launch_rbgs(const Level<T>& L, int color, bool zero_guess, cudaStream_t s);
+void launch_rbgs_sweep(const Level<T>& L, int first, bool zero_guess, const Level<T>* coarse, cudaStream_t s);
 template <class T>
 void launch_resid_restrict(const Level<T>& f, const Level<T>& c, cudaStream_t s);
-template <class T>
-void launch_prolong_add(const Level<T>& c, const Level<T>& f, cudaStream_t s);
 template <class T>
 int launch_tail(const Level<T>& L, int ncycles, int nu, cudaStream_t s);
 template <class T>

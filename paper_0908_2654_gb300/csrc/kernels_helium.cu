@@ -177,9 +177,10 @@ __global__ void __launch_bounds__(kBlock) k_assemble_he(PhysParams P, AssembleAr
         const double* st = A.step;
         auto Et = [&](long long j) { return st ? fma(lam, st[j], Ec[j]) : Ec[j]; };
         const double E = Et(i);
+        const double wb = outflow_coupling(P, A.E0, A.n0, i, x, y, z);   // outflow faces (ghost E = 0)
         const double lap = s.wxp * (Et(s.xp) - E) + s.wxm * (Et(s.xm) - E) + s.wyp * (Et(s.yp) - E) +
-                           s.wym * (Et(s.ym) - E) + s.wzp * (Et(s.zp) - E) + s.wzm * (Et(s.zm) - E);
-        const double sumw = s.wxp + s.wxm + s.wyp + s.wym + s.wzp + s.wzm;
+                           s.wym * (Et(s.ym) - E) + s.wzp * (Et(s.zp) - E) + s.wzm * (Et(s.zm) - E) - wb * E;
+        const double sumw = s.wxp + s.wxm + s.wyp + s.wym + s.wzp + s.wzm + wb;
 
         CellHe c;
         c.rho = A.rho[i];

@@ -6,9 +6,10 @@
 //  * FP64 conjugate-gradient vector kernels (matrix-vector product with fused dot product,
 //    fused x/r update with the residual norm, fused dot pairs) -- HBM-bound streams;
 //  * geometric multigrid, templated on the working precision T (float for the mixed path):
-//      - red-black Gauss-Seidel smoothing;
+//      - red-black Gauss-Seidel sweeps, each one pass over HBM on shared-memory plane tiles
+//        (smoother.cuh), the first post-smoothing sweep taking the trilinear cell-centred
+//        prolongation of the coarse correction on the fly;
 //      - fused residual + restriction (average of the 8 children);
-//      - trilinear cell-centred prolongation added to the fine correction;
 //      - coarse operators by averaging: sigma_c = geometric mean of the children's
 //        sigma = diag - sum w, coarse face coupling = sum of the 4 fine face couplings / 16
 //        (what re-discretising the diffusion term on the doubled cell gives for constant
@@ -16,6 +17,7 @@
 //      - a single-CTA solver that runs the remaining coarse levels in shared memory and finishes
 //        with a dense Cholesky solve (or the exact 1-cell solve) on the coarsest one.
 #include "kernels.cuh"
+#include "smoother.cuh"
 
 namespace {
 
@@ -249,35 +251,20 @@ __global__ void k_cg_scalars(double* scal, const double* dots, int phase) {
 // ------------------------------------------------------------------- multigrid kernels
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_rbgs(Level<T> L, int color, int zero_guess) {
-    const Dims d = L.d;
-    const int hx = d.nx / 2;
-    const long long npairs = (long long)hx * d.ny * d.nz;
-    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < npairs;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long q = t / hx;
-        const int px = (int)(t - q * hx);
-        const int z = (int)(q / d.ny);
-        const int y = (int)(q - (long long)z * d.ny);
-        const int x = 2 * px + ((y + z + color) & 1);
-        const long long i = (long long)z * sz + (long long)y * sy + x;
-        T num = L.b[i];
-        if (!zero_guess) {
-            const long long b0 = i - x - (long long)y * sy - (long long)z * sz;
-            const long long xm = b0 + dn(x, d.nx, d.per[0]) + y * sy + z * sz;
-            const long long xp = b0 + up(x, d.nx, d.per[0]) + y * sy + z * sz;
-            const long long ym = b0 + x + dn(y, d.ny, d.per[1]) * sy + z * sz;
-            const long long yp = b0 + x + up(y, d.ny, d.per[1]) * sy + z * sz;
-            const long long zm = b0 + x + y * sy + dn(z, d.nz, d.per[2]) * sz;
-            const long long zp = b0 + x + y * sy + up(z, d.nz, d.per[2]) * sz;
-            const T wxm = (!d.per[0] && x == 0) ? T(0) : L.wx[xm];
-            const T wym = (!d.per[1] && y == 0) ? T(0) : L.wy[ym];
-            const T wzm = (!d.per[2] && z == 0) ? T(0) : L.wz[zm];
-            num += L.wx[i] * L.x[xp] + wxm * L.x[xm] + L.wy[i] * L.x[yp] + wym * L.x[ym] + L.wz[i] * L.x[zp] +
-                   wzm * L.x[zm];
-        }
-        L.x[i] = num / L.diag[i];
+__global__ void __launch_bounds__(sweep::kThreads) k_rbgs_sweep(sweep::Args<T> A) {
+    extern __shared__ __align__(16) unsigned char smem_sweep[];
+    sweep::Tile<T>& S = *reinterpret_cast<sweep::Tile<T>*>(smem_sweep);
+    const int X0 = blockIdx.x * sweep::TX, Y0 = blockIdx.y * sweep::TY;
+    const int z0 = blockIdx.z * A.zc, z1 = min(z0 + A.zc, A.d.nz);
+    // plane p is staged, the first colour computed one plane behind it and the second colour
+    // two planes behind (it needs the first colour on both of its z neighbours)
+    for (int p = z0 - 2; p <= z1 + 1; ++p) {
+        sweep::load(A, S, X0, Y0, p, threadIdx.x, blockDim.x);
+        __syncthreads();
+        if (p - 1 >= z0 - 1) sweep::first_colour(A, S, X0, Y0, p - 1, z0, z1, threadIdx.x, blockDim.x);
+        __syncthreads();
+        if (p - 2 >= z0) sweep::second_colour(A, S, X0, Y0, p - 2, threadIdx.x, blockDim.x);
+        __syncthreads();
     }
 }
 
@@ -300,27 +287,6 @@ __global__ void __launch_bounds__(kBlock) k_resid_restrict(Level<T> f, Level<T> 
                     sum += f.b[i] - apply_S<T, T>(i, x, y, z, f.d, f.diag, f.wx, f.wy, f.wz, f.x);
                 }
         c.b[I] = sum * T(0.125);
-    }
-}
-
-template <class T>
-__global__ void __launch_bounds__(kBlock) k_prolong_add(Level<T> c, Level<T> f) {
-    const Dims fd = f.d, cd = c.d;
-    const long long n = fd.n();
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int x, y, z;
-        cell_coords(i, fd.nx, fd.ny, x, y, z);
-        const int X = x >> 1, Y = y >> 1, Z = z >> 1;
-        // the other coarse cell of the trilinear stencil along each axis; a wall reflects
-        const int X2 = (x & 1) ? up(X, cd.nx, cd.per[0]) : dn(X, cd.nx, cd.per[0]);
-        const int Y2 = (y & 1) ? up(Y, cd.ny, cd.per[1]) : dn(Y, cd.ny, cd.per[1]);
-        const int Z2 = (z & 1) ? up(Z, cd.nz, cd.per[2]) : dn(Z, cd.nz, cd.per[2]);
-        const long long sy = cd.nx, sz = (long long)cd.nx * cd.ny;
-        auto C = [&](int a, int b, int e) { return c.x[(long long)e * sz + (long long)b * sy + a]; };
-        const T w1 = T(0.75), w2 = T(0.25);
-        const T vz1 = w1 * (w1 * C(X, Y, Z) + w2 * C(X2, Y, Z)) + w2 * (w1 * C(X, Y2, Z) + w2 * C(X2, Y2, Z));
-        const T vz2 = w1 * (w1 * C(X, Y, Z2) + w2 * C(X2, Y, Z2)) + w2 * (w1 * C(X, Y2, Z2) + w2 * C(X2, Y2, Z2));
-        f.x[i] += w1 * vz1 + w2 * vz2;
     }
 }
 
@@ -668,17 +634,55 @@ template <class T>
 void launch_coarsen(const Level<T>& f, const Level<T>& c, cudaStream_t s) {
     k_coarsen<T><<<grid_for(c.d.n()), kBlock, 0, s>>>(f, c);
 }
+namespace {
+sweep::Geo geo_of(const Dims& d) {
+    sweep::Geo g;
+    g.nx = d.nx;
+    g.ny = d.ny;
+    g.nz = d.nz;
+    for (int k = 0; k < 3; ++k) g.per[k] = d.per[k];
+    return g;
+}
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 152;
+    }
+    return n;
+}
+}  // namespace
+
 template <class T>
-void launch_rbgs(const Level<T>& L, int color, bool zero_guess, cudaStream_t s) {
-    k_rbgs<T><<<grid_for(L.d.n() / 2), kBlock, 0, s>>>(L, color, zero_guess ? 1 : 0);
+void launch_rbgs_sweep(const Level<T>& L, int first, bool zero_guess, const Level<T>* coarse, cudaStream_t s) {
+    sweep::Args<T> A;
+    A.d = geo_of(L.d);
+    A.diag = L.diag;
+    A.wx = L.wx;
+    A.wy = L.wy;
+    A.wz = L.wz;
+    A.b = L.b;
+    A.xin = L.x;
+    A.xout = L.xt;
+    A.first = first;
+    A.zero_guess = zero_guess ? 1 : 0;
+    A.zc = sweep::chunk_planes(A.d, sm_count());
+    A.xc = coarse ? coarse->x : nullptr;
+    A.cd = coarse ? geo_of(coarse->d) : A.d;
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_rbgs_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(sweep::Tile<T>));
+        configured = true;
+    }
+    const dim3 grid((L.d.nx + sweep::TX - 1) / sweep::TX, (L.d.ny + sweep::TY - 1) / sweep::TY,
+                    (L.d.nz + A.zc - 1) / A.zc);
+    k_rbgs_sweep<T><<<grid, sweep::kThreads, sizeof(sweep::Tile<T>), s>>>(A);
 }
 template <class T>
 void launch_resid_restrict(const Level<T>& f, const Level<T>& c, cudaStream_t s) {
     k_resid_restrict<T><<<grid_for(c.d.n()), kBlock, 0, s>>>(f, c);
-}
-template <class T>
-void launch_prolong_add(const Level<T>& c, const Level<T>& f, cudaStream_t s) {
-    k_prolong_add<T><<<grid_for(f.d.n()), kBlock, 0, s>>>(c, f);
 }
 template <class T>
 size_t tail_smem_bytes(const Dims& d) {
@@ -704,12 +708,10 @@ int launch_tail(const Level<T>& L, int ncycles, int nu, cudaStream_t s) {
 
 template void launch_coarsen<float>(const Level<float>&, const Level<float>&, cudaStream_t);
 template void launch_coarsen<double>(const Level<double>&, const Level<double>&, cudaStream_t);
-template void launch_rbgs<float>(const Level<float>&, int, bool, cudaStream_t);
-template void launch_rbgs<double>(const Level<double>&, int, bool, cudaStream_t);
+template void launch_rbgs_sweep<float>(const Level<float>&, int, bool, const Level<float>*, cudaStream_t);
+template void launch_rbgs_sweep<double>(const Level<double>&, int, bool, const Level<double>*, cudaStream_t);
 template void launch_resid_restrict<float>(const Level<float>&, const Level<float>&, cudaStream_t);
 template void launch_resid_restrict<double>(const Level<double>&, const Level<double>&, cudaStream_t);
-template void launch_prolong_add<float>(const Level<float>&, const Level<float>&, cudaStream_t);
-template void launch_prolong_add<double>(const Level<double>&, const Level<double>&, cudaStream_t);
 template int launch_tail<float>(const Level<float>&, int, int, cudaStream_t);
 template int launch_tail<double>(const Level<double>&, int, int, cudaStream_t);
 template size_t tail_smem_bytes<float>(const Dims&);

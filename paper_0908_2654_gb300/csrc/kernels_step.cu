@@ -1,7 +1,9 @@
 // Per-step and per-Newton-iteration kernels of the implicit step (FP64).
 //
 //  k_faces       once per step: flux-limited face couplings w = dt theta D / (a dx)^2 on the
-//                +x/+y/+z face of every cell, D from Eq. limiter at the step's starting state.
+//                +x/+y/+z face of every cell, D from Eq. limiter at the step's starting state
+//                (0 on boundary faces; an outflow face's coupling to its empty ghost is
+//                recomputed where it is used, outflow_coupling).
 //  k_setup       once per step: explicit part b_E of Eq. radiation_residual and the initial
 //                iterate (E* + dt 4 pi eta, n_HI*, 0).
 //  k_assemble    once per Newton trial, fused: trial E = E_k + lam s, exact solution of the
@@ -82,7 +84,8 @@ __global__ void k_setup(PhysParams P, const double* __restrict__ E0, const doubl
         const Stencil s = stencil(i, x, y, z, P.nx, P.ny, P.nz, P.per, wx, wy, wz);
         const double E = E0[i];
         const double lap = s.wxp * (E0[s.xp] - E) + s.wxm * (E0[s.xm] - E) + s.wyp * (E0[s.yp] - E) +
-                           s.wym * (E0[s.ym] - E) + s.wzp * (E0[s.zp] - E) + s.wzm * (E0[s.zm] - E);
+                           s.wym * (E0[s.ym] - E) + s.wzp * (E0[s.zp] - E) + s.wzm * (E0[s.zm] - E) -
+                           outflow_coupling(P, E0, n0, i, x, y, z) * E;
         const double kap = kappa_start(P, n0, i);
         bE[i] = E + expl * lap + P.dt * (1.0 - P.theta) * (-P.H * E + src[i] - P.c * kap * E);
         const double Ei = E + P.dt * src[i];
@@ -189,9 +192,10 @@ __global__ void __launch_bounds__(kBlock) k_assemble(PhysParams P, AssembleArgs 
         const double* st = A.step;
         auto Et = [&](long long j) { return st ? fma(lam, st[j], Ec[j]) : Ec[j]; };
         const double E = Et(i);
+        const double wb = outflow_coupling(P, A.E0, A.n0, i, x, y, z);   // outflow faces (ghost E = 0)
         const double lap = s.wxp * (Et(s.xp) - E) + s.wxm * (Et(s.xm) - E) + s.wyp * (Et(s.yp) - E) +
-                           s.wym * (Et(s.ym) - E) + s.wzp * (Et(s.zp) - E) + s.wzm * (Et(s.zm) - E);
-        const double sumw = s.wxp + s.wxm + s.wyp + s.wym + s.wzp + s.wzm;
+                           s.wym * (Et(s.ym) - E) + s.wzp * (Et(s.zp) - E) + s.wzm * (Et(s.zm) - E) - wb * E;
+        const double sumw = s.wxp + s.wxm + s.wyp + s.wym + s.wzp + s.wzm + wb;
 
         CellIn c;
         c.rho = A.rho[i];

@@ -45,6 +45,7 @@ struct PhysParams {
     // grid
     int nx, ny, nz;
     int per[3];
+    int outflow[6];    // per face (x-, x+, y-, y+, z-, z+): 1 = outflow boundary face
     double dx;         // comoving cell width (normalised)
     // step
     double a, a3, H;   // expansion factor, a^3, adot / a (per normalised time)
@@ -316,4 +317,22 @@ RT_HD double limiter_face(const PhysParams& P, double Ei, double Ej, double ki, 
     double kT = 0.5 * (ki + kj);
     if (kT == 0.0 && R == 0.0) R = 1.0 / P.adx;
     return P.c * (2.0 * kT + R) / ((6.0 * kT + 3.0 * R) * kT + R * R);
+}
+
+// Number of outflow boundary faces of cell (x, y, z) (0 for interior cells).
+RT_HD int outflow_faces(const PhysParams& P, int x, int y, int z) {
+    return (P.outflow[0] && x == 0) + (P.outflow[1] && x == P.nx - 1) + (P.outflow[2] && y == 0) +
+           (P.outflow[3] && y == P.ny - 1) + (P.outflow[4] && z == 0) + (P.outflow[5] && z == P.nz - 1);
+}
+
+// Face coupling summed over the outflow faces of cell i: each face joins the cell to an empty
+// ghost (E = 0, the cell's own opacity), so it couples w = dt theta D / (a dx)^2 with D from
+// Eq. limiter between the two, evaluated at the step's start like every face (lagged limiter).
+// Its flux w (0 - E) only removes energy: it adds w to the cell's diagonal and nothing off it.
+RT_HD double outflow_coupling(const PhysParams& P, const double* E0, const double* n0, long long i, int x, int y,
+                              int z) {
+    const int nf = outflow_faces(P, x, y, z);
+    if (nf == 0) return 0.0;
+    const double ki = kappa_start(P, n0, i);
+    return nf * P.wscale * limiter_face(P, E0[i], 0.0, ki, ki);
 }

@@ -16,6 +16,15 @@ from .units import Units, specific_energy
 
 _SPECTRA = {"mono": _rt.RT_SPECTRUM_MONO, "blackbody": _rt.RT_SPECTRUM_BLACKBODY}
 _RECOMB = {"const": _rt.RT_RECOMB_CONST, "hg97": _rt.RT_RECOMB_HG97}
+_BC = {"periodic": _rt.RT_BC_PERIODIC, "reflect": _rt.RT_BC_REFLECT, "outflow": _rt.RT_BC_OUTFLOW}
+
+
+def _faces(w):
+    """Boundary type of the six faces (x-, x+, y-, y+, z-, z+) of workload w: its ``bc`` entry, or
+    from ``periodic`` (non-periodic axes reflect at both faces)."""
+    if w.get("bc") is not None:
+        return tuple(w["bc"])
+    return tuple(t for p in w["periodic"] for t in (("periodic",) * 2 if p else ("reflect",) * 2))
 
 
 class Solver:
@@ -41,8 +50,8 @@ class Solver:
         d = _rt.GridDesc()
         d.nx, d.ny, d.nz = nx, ny, nz
         d.dx = w["dx"] / u.u_x
-        for k in range(3):
-            d.bc[k] = _rt.RT_BC_PERIODIC if w["periodic"][k] else _rt.RT_BC_WALL
+        for f, kind in enumerate(_faces(w)):
+            d.bc[f] = _BC[kind]
         d.u_x, d.u_t, d.u_g = u.u_x, u.u_t, u.u_g
         d.theta = self.theta
         d.precision = _rt.RT_MIXED if precision == "mixed" else _rt.RT_FP64

@@ -32,7 +32,7 @@ def _desc(**kw):
     d = _rt.GridDesc()
     d.nx = d.ny = d.nz = 8
     d.dx = 1.0
-    for k in range(3):
+    for k in range(6):
         d.bc[k] = _rt.RT_BC_PERIODIC
     d.u_x = d.u_t = d.u_g = 1.0
     d.theta = 0.51
@@ -60,7 +60,8 @@ def _desc(**kw):
 nan = float("nan")
 BAD_DESCRIPTORS = [
     dict(nx=0), dict(nz=-4), dict(dx=0.0), dict(dx=-1.0), dict(dx=nan), dict(u_x=0.0), dict(u_t=nan),
-    dict(u_g=-1.0), dict(theta=0.0), dict(theta=1.5), dict(theta=nan), dict(bc=(0, 7, 0)),
+    dict(u_g=-1.0), dict(theta=0.0), dict(theta=1.5), dict(theta=nan), dict(bc=(0, 0, 7, 7, 0, 0)),
+    dict(bc=(0, 1, 0, 0, 0, 0)), dict(bc=(2, 0, 0, 0, 0, 0)), dict(bc=(0, 0, 0, 0, 1, -1)),
     dict(precision=5), dict(mg_nu1=0), dict(mg_nu2=0), dict(max_newton=0), dict(max_lin=0),
     dict(newton_tol=0.0), dict(newton_tol=nan), dict(lin_rtol=-1.0), dict(helium=2),
     dict(helium=1, Y=1.0), dict(helium=1, Y=-0.1), dict(helium=1, Y=nan),

@@ -19,7 +19,9 @@ def _res():
         "cg_spmv_dot": dict(launches=140, ms=37.0, bytes=1.1e11),
     }
     stats = [dict(newton_iters=4, linear_iters=35, kernel_launches=2970) for _ in range(4)]
-    return dict(value=5.6e7, ms=1190.0, stats=stats, prof=prof, fp64={"value": 4.1e7},
+    return dict(value=5.6e7, ms=1190.0, stats=stats, prof=prof, fp64={"value": 4.1e7, "ms_per_step": 409.0, "speedup_mixed_vs_fp64": 1.37,
+                                                           "newton_iters": [4] * 4, "linear_iters": [30] * 4,
+                                                           "mixed_vs_fp64_error": {"E_rel_2": 1e-11}},
                 clocks={"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []},
                 e2e={"value": 5.1e7, "unit": "cell-steps/s", "h2d_bytes_per_step": 1, "d2h_bytes_per_step": 1},
                 w=None, advect={"advect": dict(launches=10, ms=16.3, bytes=10 * 72.0 * 256**3), "courant_max": 0.05})
@@ -42,6 +44,11 @@ def test_bench_line_contract_and_rooflines():
     assert mg["fine_level"]["frac"] == pytest.approx(mg["fine_level"]["achieved"] / 6797.2)
     assert line["gpu_launches"] == 4 * 2970 + 4
     assert line["ms_per_step"] == pytest.approx(1190.0 / 4)
+    # the FP64 arm and the per-kernel shares sit in the config block
+    cfg = line["config"]
+    assert cfg["fp64_path"]["speedup_mixed_vs_fp64"] == 1.37 and cfg["mixed_vs_fp64_error"]["E_rel_2"] == 1e-11
+    assert cfg["kernel_shares"]["newton_assemble"][0] == pytest.approx(700.0 / 1190.0, abs=1e-4)
+    assert cfg["vcycle_smoother"]["fine_level"]["achieved"] == pytest.approx(mg["fine_level"]["achieved"])
     json.loads(json.dumps(line))
 
 
