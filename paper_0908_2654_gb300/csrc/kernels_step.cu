@@ -13,6 +13,7 @@
 //                the component-scaled RMS norm (Eq. rmsnorm).
 #include "cellgrid.cuh"
 #include "kernels.cuh"
+#include "hlocal.cuh"
 
 namespace {
 
@@ -113,17 +114,16 @@ struct LocalOut {
 };
 
 template <bool ISO, bool GIVEN>
-__device__ __forceinline__ LocalOut local_block(const PhysParams& P, const CellIn& c, double E, double ec_in,
-                                                double n_in, double se) {
+__device__ __forceinline__ LocalOut local_block(const PhysParams& P, const HCell& c, double E, double ec_in,
+                                                double n_in, double inv_se, double inv_rho) {
     LocalOut o;
     if (ISO) {
-        Dual<1> Se, Sn;
-        local_solutions<Dual<1>>(P, c, dconst<1>(0.0), dconst<1>(n_in), dvar<1>(E, 0), Se, Sn);
+        const HLocal L = h_local<true>(P, c, 0.0, n_in, E);
         o.ec = GIVEN ? ec_in : 0.0;
-        o.n = GIVEN ? n_in : Sn.v;
+        o.n = GIVEN ? n_in : L.Sn;
         o.fe = o.ec;
-        o.fn = o.n - Sn.v;
-        o.X = -Sn.d[0];
+        o.fn = o.n - L.Sn;
+        o.X = -L.Sn_E;
         o.Y = o.fn;
         o.Xe = 0.0;
         return o;
@@ -132,30 +132,27 @@ __device__ __forceinline__ LocalOut local_block(const PhysParams& P, const CellI
     // keeping 0 < n_HI <= n_H and the internal energy positive
     double ec = ec_in, n = n_in;
     if (!GIVEN) n = fmin(fmax(n, 1e-300), c.rho);
-    Dual<3> Se, Sn;
-    local_solutions<Dual<3>>(P, c, dvar<3>(ec, 0), dvar<3>(n, 1), dvar<3>(E, 2), Se, Sn);
-    double fe = ec - Se.v, fn = n - Sn.v;
-    double r = fmax(fabs(fe) / se, fabs(fn) / c.rho);
+    HLocal L = h_local<false>(P, c, ec, n, E);
+    double fe = ec - L.Se, fn = n - L.Sn;
+    double r = fmax(fabs(fe) * inv_se, fabs(fn) * inv_rho);
     const int maxit = GIVEN ? 0 : 60;
     for (int it = 0; it < maxit && r > P.local_tol; ++it) {
-        const double a11 = 1.0 - Se.d[0], a12 = -Se.d[1], a21 = -Sn.d[0], a22 = 1.0 - Sn.d[1];
-        const double det = a11 * a22 - a12 * a21;
-        const double de = -(a22 * fe - a12 * fn) / det;
-        const double dn_ = -(a11 * fn - a21 * fe) / det;
+        const double a11 = 1.0 - L.Se_e, a12 = -L.Se_n, a21 = -L.Sn_e, a22 = 1.0 - L.Sn_n;
+        const double idet = 1.0 / (a11 * a22 - a12 * a21);
+        const double de = -(a22 * fe - a12 * fn) * idet;
+        const double dn_ = -(a11 * fn - a21 * fe) * idet;
         double lam = 1.0;
         bool moved = false;
         for (int k = 0; k < 40; ++k, lam *= 0.5) {
             const double ec_t = fmax(ec + lam * de, -0.999 * c.eh_kin);
             const double n_t = fmin(fmax(n + lam * dn_, 1e-300), c.rho);
-            Dual<3> Se_t, Sn_t;
-            local_solutions<Dual<3>>(P, c, dvar<3>(ec_t, 0), dvar<3>(n_t, 1), dvar<3>(E, 2), Se_t, Sn_t);
-            const double fe_t = ec_t - Se_t.v, fn_t = n_t - Sn_t.v;
-            const double r_t = fmax(fabs(fe_t) / se, fabs(fn_t) / c.rho);
+            const HLocal Lt = h_local<false>(P, c, ec_t, n_t, E);
+            const double fe_t = ec_t - Lt.Se, fn_t = n_t - Lt.Sn;
+            const double r_t = fmax(fabs(fe_t) * inv_se, fabs(fn_t) * inv_rho);
             if (r_t < r) {
                 ec = ec_t;
                 n = n_t;
-                Se = Se_t;
-                Sn = Sn_t;
+                L = Lt;
                 fe = fe_t;
                 fn = fn_t;
                 r = r_t;
@@ -165,23 +162,25 @@ __device__ __forceinline__ LocalOut local_block(const PhysParams& P, const CellI
         }
         if (!moved) break;   // round-off floor
     }
-    const double a11 = 1.0 - Se.d[0], a21 = -Sn.d[0];
-    const double a12 = -Se.d[1], a22 = 1.0 - Sn.d[1];
-    const double det = a11 * a22 - a12 * a21;
-    const double be = -Se.d[2], bn = -Sn.d[2];
+    const double a11 = 1.0 - L.Se_e, a21 = -L.Sn_e;
+    const double a12 = -L.Se_n, a22 = 1.0 - L.Sn_n;
+    const double idet = 1.0 / (a11 * a22 - a12 * a21);
+    const double be = -L.Se_E, bn = -L.Sn_E;
     o.ec = ec;
     o.n = n;
     o.fe = fe;
     o.fn = fn;
-    o.X = (a11 * bn - a21 * be) / det;
-    o.Y = (a11 * fn - a21 * fe) / det;
-    o.Xe = (a22 * be - a12 * bn) / det;
+    o.X = (a11 * bn - a21 * be) * idet;
+    o.Y = (a11 * fn - a21 * fe) * idet;
+    o.Xe = (a22 * be - a12 * bn) * idet;
     return o;
 }
 
 template <bool ISO, bool GIVEN>
 __global__ void __launch_bounds__(kBlock) k_assemble(PhysParams P, AssembleArgs A) {
     const long long n = (long long)P.nx * P.ny * P.nz;
+    const double inv_a3 = 1.0 / P.a3;
+    const double kEa = P.kE * inv_a3;     // proper opacity per unit n_HI
     double acc[3] = {0.0, 0.0, 0.0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         int x, y, z;
@@ -197,17 +196,14 @@ __global__ void __launch_bounds__(kBlock) k_assemble(PhysParams P, AssembleArgs 
                            s.wym * (Et(s.ym) - E) + s.wzp * (Et(s.zp) - E) + s.wzm * (Et(s.zm) - E) - wb * E;
         const double sumw = s.wxp + s.wxm + s.wyp + s.wym + s.wzp + s.wzm + wb;
 
-        CellIn c;
-        c.rho = A.rho[i];
-        c.nHI0 = A.n0[i];
-        c.E0 = A.E0[i];
         double v2 = 0.0;
         if (A.vx) v2 += A.vx[i] * A.vx[i];
         if (A.vy) v2 += A.vy[i] * A.vy[i];
         if (A.vz) v2 += A.vz[i] * A.vz[i];
-        c.eh_kin = A.e_h[i] - 0.5 * v2;
-        c.clump = A.clump ? (double)A.clump[i] : 1.0;
+        const HCell c = make_hcell(P, inv_a3, A.rho[i], A.n0[i], A.E0[i], A.e_h[i] - 0.5 * v2,
+                                   A.clump ? (double)A.clump[i] : 1.0);
         const double se = fmax(c.eh_kin, P.e_floor);
+        const double inv_se = 1.0 / se, inv_rho = 1.0 / c.rho;
 
         double ec_in = GIVEN ? A.ec_given[i] : (A.ec_guess ? A.ec_guess[i] : 0.0);
         double n_in = GIVEN ? A.n_given[i] : A.n_guess[i];
@@ -217,19 +213,19 @@ __global__ void __launch_bounds__(kBlock) k_assemble(PhysParams P, AssembleArgs 
             ec_in = fmax(ec_in - A.Xe_cur[i] * dE, -0.999 * c.eh_kin);
             n_in = fmin(fmax(n_in - A.Xn_cur[i] * dE, 1e-300), c.rho);
         }
-        const LocalOut L = local_block<ISO, GIVEN>(P, c, E, ec_in, n_in, se);
+        const LocalOut L = local_block<ISO, GIVEN>(P, c, E, ec_in, n_in, inv_se, inv_rho);
 
-        const double kap = P.kE * L.n / P.a3;
+        const double kap = kEa * L.n;
         const double dtt = P.dt * P.theta;
         const double fE = E - A.bE[i] - lap - dtt * (-P.H * E + A.src[i] - P.c * kap * E);
-        const double AEn = dtt * P.c * P.kE * E / P.a3;
+        const double AEn = dtt * P.c * kEa * E;
         const double AEE = 1.0 + dtt * (P.H + P.c * kap) + sumw;
         const double dg = AEE - AEn * L.X;
         const double rh = -fE + AEn * L.Y;
 
         const double wEc = 1.0 / fmax(fmax(fabs(Ec[i]), c.E0), P.E_floor);
         const double wEt = 1.0 / fmax(fmax(fabs(E), c.E0), P.E_floor);
-        const double loc = (L.fn / c.rho) * (L.fn / c.rho) + (L.fe / se) * (L.fe / se);
+        const double loc = (L.fn * inv_rho) * (L.fn * inv_rho) + (L.fe * inv_se) * (L.fe * inv_se);
         acc[0] += (wEc * fE) * (wEc * fE) + loc;
         acc[1] += (wEt * fE) * (wEt * fE) + loc;
         if (!isfinite(fE) || !isfinite(dg) || !isfinite(L.n) || !isfinite(L.ec)) acc[2] += 1.0;
