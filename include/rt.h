@@ -156,6 +156,9 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out);
  * stats may be NULL.  It describes the attempt on success, on RT_ENOCONV and RT_ELINESEARCH,
  * and on any error the linear solve returns.  It is left as the caller passed it on argument
  * errors, on a non-finite residual evaluation and on CUDA errors outside the linear solve.
+ * The hydro state in `in` is checked on the device first: a density that is not positive and
+ * finite, a non-finite energy or (non-isothermal grids) a non-positive internal energy
+ * e_h - |v|^2/2 in any cell gives RT_EINVAL before anything is written.
  * Errors: RT_EINVAL, RT_ENOCONV, RT_ELINESEARCH, RT_ENONFINITE, RT_ELINEAR,
  * RT_ECUDA; *inout is unchanged on error. */
 int rt_implicit_step(rt_grid* g, const rt_step_inputs* in, rt_state* inout, rt_step_stats* stats);

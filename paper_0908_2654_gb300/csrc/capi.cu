@@ -588,8 +588,10 @@ int step_setup(rt_grid* g, const rt_step_inputs* in, PhysParams& P, const double
     run(g, K_FACES, N * (g->wxf ? 52 : 40),
         [&] { launch_faces(P, g->E0, g->n0, g->wx, g->wy, g->wz, g->wxf, g->wyf, g->wzf, s); });
     int nb = 0;
-    run(g, K_SETUP, N * 80, [&] {
-        nb = launch_setup(P, g->E0, g->n0, g->src, g->wx, g->wy, g->wz, g->bE, g->Ec, g->nc, g->ecc, g->partials, s);
+    const HydroIn hy = {in->rho_b, in->e_h, in->vx, in->vy, in->vz};
+    run(g, K_SETUP, N * (96 + (in->vx ? 24 : 0)), [&] {
+        nb = launch_setup(P, g->E0, g->n0, g->src, g->wx, g->wy, g->wz, g->bE, g->Ec, g->nc, g->ecc, g->partials, hy,
+                          g->d_err, s);
     });
     run(g, K_FINALIZE, 0.0, [&] { launch_finalize_ext(g->partials, nb, 0, 1, g->dots, s); });
     int herr = 0;
@@ -598,8 +600,13 @@ int step_setup(rt_grid* g, const rt_step_inputs* in, PhysParams& P, const double
     RT_CUDA(cudaStreamSynchronize(s));
     std::memcpy(&herr, &g->h_pinned[0], sizeof(int));
     P.E_floor = std::max(P.E_min, 1e-12 * g->h_pinned[1]);
-    if (herr) {
+    if (herr & 1) {
         set_detail("a source cell index is outside the grid");
+        return RT_EINVAL;
+    }
+    if (herr & 2) {
+        set_detail("invalid hydro state: a density that is not positive and finite, a non-finite energy, or a "
+                   "non-positive internal energy of non-isothermal gas");
         return RT_EINVAL;
     }
     return check_launch("step setup");

@@ -20,14 +20,25 @@ struct Dims {
 
 // ---- step setup
 void launch_zero(double* p, long long n, cudaStream_t s);
+// sets bit 1 of *d_err for a source index outside the grid (that source is skipped)
 void launch_scatter_sources(double* src, const int64_t* cell, const double* ndot, int nsrc, double scale,
                             long long ncell, int* d_err, cudaStream_t s);
 void launch_faces(const PhysParams& P, const double* E0, const double* n0, double* wx, double* wy, double* wz,
                   float* wxf, float* wyf, float* wzf, cudaStream_t s);
-// also writes per-block max |E_init| to partials (one slot); returns the number of blocks
+// the hydro state of the step (device pointers; velocities may be null)
+struct HydroIn {
+    const double* rho;
+    const double* e_h;
+    const double* vx;
+    const double* vy;
+    const double* vz;
+};
+// also writes per-block max |E_init| to partials (one slot) and sets bit 2 of *err where the
+// hydro state is invalid (density not positive and finite, energy not finite, non-isothermal
+// internal energy not positive); returns the number of blocks
 int launch_setup(const PhysParams& P, const double* E0, const double* n0, const double* src, const double* wx,
                  const double* wy, const double* wz, double* bE, double* E_init, double* n_init, double* ec_init,
-                 double* partials, cudaStream_t s);
+                 double* partials, const HydroIn& H, int* err, cudaStream_t s);
 
 // ---- fused Newton evaluation
 struct AssembleArgs {

@@ -376,12 +376,23 @@ __host__ __device__ inline void make_plan(const Dims& top, TailPlan& p) {
 }
 
 // one colour of a red-black Gauss-Seidel sweep on a shared-memory level: the new value is
-// (b + sum of the neighbours' couplings) / diag; the cell's own previous value is not read
+// (b + sum of the neighbours' couplings) / diag; the cell's own previous value is not read.
+// All new values of the colour are computed before any is stored, so on a periodic axis of odd
+// length (where cells 0 and n-1 share a colour and are neighbours) both see each other's old
+// value and the result does not depend on thread timing; with a proper two-colouring this is
+// the same sweep.  Levels hold at most kTailCellsPerThread * blockDim.x cells.
+constexpr int kTailCellsPerThread = 4;
+
 template <class T>
 __device__ void tail_smooth(const Dims& d, T* diag, T* wx, T* wy, T* wz, T* x, const T* b, int color, bool zero) {
     const long long n = d.n();
     const long long sy = d.nx, sz = (long long)d.nx * d.ny;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    T nv[kTailCellsPerThread];
+#pragma unroll
+    for (int k = 0; k < kTailCellsPerThread; ++k) {
+        const long long i = threadIdx.x + (long long)k * blockDim.x;
+        nv[k] = T(0);
+        if (i >= n) continue;
         int cx, cy, cz;
         cell_coords(i, d.nx, d.ny, cx, cy, cz);
         if (((cx + cy + cz) & 1) != color) continue;
@@ -399,7 +410,16 @@ __device__ void tail_smooth(const Dims& d, T* diag, T* wx, T* wy, T* wz, T* x, c
             const T wzm = (!d.per[2] && cz == 0) ? T(0) : wz[zm];
             num += wx[i] * x[xp] + wxm * x[xm] + wy[i] * x[yp] + wym * x[ym] + wz[i] * x[zp] + wzm * x[zm];
         }
-        x[i] = num / diag[i];
+        nv[k] = num / diag[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kTailCellsPerThread; ++k) {
+        const long long i = threadIdx.x + (long long)k * blockDim.x;
+        if (i >= n) continue;
+        int cx, cy, cz;
+        cell_coords(i, d.nx, d.ny, cx, cy, cz);
+        if (((cx + cy + cz) & 1) == color) x[i] = nv[k];
     }
 }
 
@@ -692,6 +712,10 @@ size_t tail_smem_bytes(const Dims& d) {
     if (p.dense) cells += (size_t)kDenseMax * kDenseMax + kDenseMax;
     return cells * sizeof(T);
 }
+static_assert(TailMax<float>::value <= kTailCellsPerThread * kTailThreads &&
+                  TailMax<double>::value <= kTailCellsPerThread * kTailThreads,
+              "a tail level must fit the per-thread cells of tail_smooth");
+
 template <class T>
 int launch_tail(const Level<T>& L, int ncycles, int nu, cudaStream_t s) {
     TailPlan p;

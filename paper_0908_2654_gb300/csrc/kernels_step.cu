@@ -30,7 +30,7 @@ __global__ void k_scatter(double* src, const int64_t* cell, const double* ndot, 
     if (k >= nsrc) return;
     long long c = cell[k];
     if (c < 0 || c >= ncell) {      // checked: an out-of-range source index is reported, not written
-        atomicExch(err, 1);
+        atomicOr(err, 1);
         return;
     }
     atomicAdd(&src[c], scale * ndot[k]);
@@ -75,11 +75,22 @@ __global__ void k_faces(PhysParams P, const double* __restrict__ E0, const doubl
 __global__ void k_setup(PhysParams P, const double* __restrict__ E0, const double* __restrict__ n0,
                         const double* __restrict__ src, const double* __restrict__ wx, const double* __restrict__ wy,
                         const double* __restrict__ wz, double* __restrict__ bE, double* __restrict__ E_init,
-                        double* __restrict__ n_init, double* __restrict__ ec_init, double* partials) {
+                        double* __restrict__ n_init, double* __restrict__ ec_init, double* partials, HydroIn H,
+                        int* err) {
     const long long n = (long long)P.nx * P.ny * P.nz;
     const double expl = (1.0 - P.theta) / P.theta;   // (1-theta) dt D/(a dx)^2 = expl * w
     double emax = 0.0;
+    bool bad = false;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        // the hydro state handed over by the operator split: positive finite density, finite
+        // energy and (non-isothermal gas) a positive internal energy
+        const double rho = H.rho[i], eh = H.e_h[i];
+        double v2 = 0.0;
+        if (H.vx) v2 += H.vx[i] * H.vx[i];
+        if (H.vy) v2 += H.vy[i] * H.vy[i];
+        if (H.vz) v2 += H.vz[i] * H.vz[i];
+        if (!(rho > 0.0) || !isfinite(rho) || !isfinite(eh) || !isfinite(v2) || (!P.isothermal && !(eh - 0.5 * v2 > 0.0)))
+            bad = true;
         int x, y, z;
         cell_coords(i, P.nx, P.ny, x, y, z);
         const Stencil s = stencil(i, x, y, z, P.nx, P.ny, P.nz, P.per, wx, wy, wz);
@@ -95,6 +106,7 @@ __global__ void k_setup(PhysParams P, const double* __restrict__ E0, const doubl
         ec_init[i] = 0.0;
         emax = fmax(emax, fabs(Ei));
     }
+    if (bad) atomicOr(err, 2);
     __shared__ double sh[kBlock / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, o));
@@ -340,10 +352,10 @@ void launch_faces(const PhysParams& P, const double* E0, const double* n0, doubl
 
 int launch_setup(const PhysParams& P, const double* E0, const double* n0, const double* src, const double* wx,
                  const double* wy, const double* wz, double* bE, double* E_init, double* n_init, double* ec_init,
-                 double* partials, cudaStream_t s) {
+                 double* partials, const HydroIn& H, int* err, cudaStream_t s) {
     const long long n = (long long)P.nx * P.ny * P.nz;
     const int g = grid_for(n);
-    k_setup<<<g, kBlock, 0, s>>>(P, E0, n0, src, wx, wy, wz, bE, E_init, n_init, ec_init, partials);
+    k_setup<<<g, kBlock, 0, s>>>(P, E0, n0, src, wx, wy, wz, bE, E_init, n_init, ec_init, partials, H, err);
     return g;
 }
 

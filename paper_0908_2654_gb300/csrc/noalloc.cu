@@ -123,7 +123,8 @@ int residual_on_device(const rt_grid_desc* desc, const rt_step_inputs* in, const
     launch_zero(src, n, s);
     launch_scatter_sources(src, in->src_cell, in->src_ndot, in->nsrc, P.src_scale, n, err, s);
     launch_faces(P, U_n->E, U_n->n_HI, wx, wy, wz, nullptr, nullptr, nullptr, s);
-    launch_setup(P, U_n->E, U_n->n_HI, src, wx, wy, wz, bE, Ei, ni, eci, partials, s);
+    const HydroIn hy = {in->rho_b, in->e_h, in->vx, in->vy, in->vz};
+    launch_setup(P, U_n->E, U_n->n_HI, src, wx, wy, wz, bE, Ei, ni, eci, partials, hy, err, s);
     AssembleArgs A;
     std::memset(&A, 0, sizeof(A));
     A.E_cur = U->E;
@@ -153,8 +154,12 @@ int residual_on_device(const rt_grid_desc* desc, const rt_step_inputs* in, const
         rt_internal_set_detail("CUDA error in rt_residual_static");
         return RT_ECUDA;
     }
-    if (herr) {
+    if (herr & 1) {
         rt_internal_set_detail("a source cell index is outside the grid");
+        return RT_EINVAL;
+    }
+    if (herr & 2) {
+        rt_internal_set_detail("invalid hydro state (density, energy or internal energy)");
         return RT_EINVAL;
     }
     if (cudaGetLastError() != cudaSuccess) {

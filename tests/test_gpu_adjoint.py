@@ -1,6 +1,7 @@
 """The CUDA discrete adjoint (rt_adjoint_step behind a torch.autograd.Function) against the
-oracle's dense adjoint on tiny grids and against central finite differences of the GPU forward
-run on 8 source emissivities."""
+oracle's dense adjoint on 8^3 grids and against central finite differences of the GPU forward
+run on 8 source emissivities.  The adjoint covers periodic and reflecting faces (the Stromgren
+case here reflects at every face); a grid with outflow faces is rejected."""
 import numpy as np
 import pytest
 
@@ -23,9 +24,9 @@ def _grad(w, nsteps, **opt):
 
 
 @pytest.mark.parametrize("name,make,nsteps", [
-    ("reion6_nonisothermal", lambda: W.reionization_field(n=6, nsrc=2, box_mpc=14.4 * 6 / 256, ndot_total=4e49,
+    ("reion8_nonisothermal", lambda: W.reionization_field(n=8, nsrc=2, box_mpc=14.4 * 8 / 256, ndot_total=4e49,
                                                           dt_myr=0.3), 2),
-    ("stromgren6_isothermal", lambda: W.stromgren_static(n=6, dt_over_trec=1e-3), 2),
+    ("stromgren8_isothermal", lambda: W.stromgren_static(n=8, dt_over_trec=1e-3, bc=("reflect",) * 6), 2),
 ])
 def test_adjoint_matches_oracle_dense_adjoint(name, make, nsteps):
     w = make()
@@ -55,3 +56,11 @@ def test_adjoint_matches_finite_differences_on_8_emissivities():
             vals.append(float(ionized_fraction(torch.tensor(p), clump, w, nsteps, **opt)))
         fd = (vals[0] - vals[1]) / (2 * h)
         assert g_ndot[s] == pytest.approx(fd, rel=1e-5), (s, g_ndot[s], fd)
+
+
+def test_adjoint_rejects_outflow_faces():
+    from paper_0908_2654_gb300 import _rt
+    w = W.stromgren_static(n=8, dt_over_trec=1e-3)          # outflow at the upper faces
+    with pytest.raises(_rt.RTError) as e:
+        _grad(w, 1, **TIGHT)
+    assert e.value.code == _rt.RT_EINVAL

@@ -108,6 +108,25 @@ def test_non_finite_input_is_rejected_and_state_kept():
     s.close()
 
 
+@pytest.mark.parametrize("field,value", [("rho", 0.0), ("rho", -1.0), ("rho", float("nan")), ("e_h", float("nan")),
+                                         ("e_h", -1e3)])
+def test_invalid_hydro_state_is_rejected_and_state_kept(field, value):
+    """The hydro state handed over by the operator split is checked on the device before any
+    state is touched: density positive and finite, energy finite, internal energy of
+    non-isothermal gas positive."""
+    from paper_0908_2654_gb300 import _rt
+    from paper_0908_2654_gb300.solver import Solver
+    w = W.random_state((8, 6, 4), seed=2, isothermal=False)
+    s = Solver(w, precision="fp64", newton_tol=1e-10, lin_rtol=1e-10)
+    getattr(s, field)[1, 2, 3] = value if field == "rho" or value != value else value * float(s.e_h.abs().max())
+    E0, n0 = s.E.clone(), s.nHI.clone()
+    with pytest.raises(_rt.RTError) as e:
+        s.step()
+    assert e.value.code == _rt.RT_EINVAL and "hydro state" in str(e.value)
+    assert torch.equal(s.E, E0) and torch.equal(s.nHI, n0)
+    s.close()
+
+
 def test_newton_iteration_cap_reports_no_convergence_and_keeps_state():
     from paper_0908_2654_gb300 import _rt
     from paper_0908_2654_gb300.solver import Solver

@@ -150,6 +150,26 @@ def test_schur_solve_matches_direct_solve(name, make, precision):
     assert its < 100
 
 
+def test_schur_solve_is_deterministic_on_odd_periodic_axes():
+    """On periodic axes of odd length two neighbouring cells share a colour; the coarse solver
+    updates each colour from the old values of all cells, so repeated solves agree bit for bit
+    (same iterations, same result)."""
+    w = W.random_state((9, 6, 5), seed=4, isothermal=True)
+    st = driver.Run(w).make_step()
+    U = N.local_solve(st, N.initial_iterate(st))
+    b = np.random.default_rng(9).standard_normal(st.shape)
+    out = []
+    for precision in ("fp64", "mixed"):
+        s = _solver(w, precision=precision)
+        s.schur_system((st.E_n, st.nHI_n), U)
+        runs = [s.schur_solve(b, rtol=1e-12, max_iters=300) for _ in range(3)]
+        s.close()
+        for x, its in runs[1:]:
+            assert its == runs[0][1] and np.array_equal(x, runs[0][0]), precision
+        out.append(runs[0][0])
+    np.testing.assert_allclose(out[0], out[1], rtol=1e-9, atol=1e-9 * np.abs(out[0]).max())
+
+
 _SOLVE_CACHE = {}
 _STEP_CACHE = {}
 
