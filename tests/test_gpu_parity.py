@@ -11,8 +11,9 @@ Tolerances:
     the stopping test:
       - 1e-10 relative on E in every cell whose E is above the norm's floor
         (max(E_min, 1e-12 of the brightest cell): below it a cell's E is round-off of the
-        bright cells' arithmetic), on x_HI relative to itself, and on e_c relative to the
-        hydro state's internal energy;
+        bright cells' arithmetic), on x_HI relative to max(x_HI, 1e-4) (the stopping test
+        scales f_n by n_H, so n_HI is resolved to about the tolerance times n_H), and on e_c
+        relative to the hydro state's internal energy;
       - 1e-9 in the component-scaled norm on every cell (floor cells included).
 """
 
@@ -202,7 +203,9 @@ def _compare(st, U, ec, n, E, worst):
     bright = np.abs(U[2]) > _floor_E(st)
     if np.any(bright):
         worst["E_rel"] = max(worst["E_rel"], float(np.max(np.abs(E - U[2])[bright] / np.abs(U[2])[bright])))
-    worst["x_rel"] = max(worst["x_rel"], float(np.max(np.abs(n - U[1]) / U[1])))
+    # x_HI relative to itself down to x_HI = 1e-4: the stopping test scales f_n by n_H, so the
+    # attainable relative accuracy of n_HI is about the tolerance over x_HI
+    worst["x_rel"] = max(worst["x_rel"], float(np.max(np.abs(n - U[1]) / np.maximum(U[1], 1e-4 * st.n_H))))
 
 
 def _step_both(name, w, nsteps, precision, tol=1e-12, reset=True):
