@@ -254,17 +254,24 @@ template <class T>
 __global__ void __launch_bounds__(sweep::kThreads) k_rbgs_sweep(sweep::Args<T> A) {
     extern __shared__ __align__(16) unsigned char smem_sweep[];
     sweep::Tile<T>& S = *reinterpret_cast<sweep::Tile<T>*>(smem_sweep);
-    const int X0 = blockIdx.x * sweep::TX, Y0 = blockIdx.y * sweep::TY;
-    const int z0 = blockIdx.z * A.zc, z1 = min(z0 + A.zc, A.d.nz);
-    // plane p is staged, the first colour computed one plane behind it and the second colour
-    // two planes behind (it needs the first colour on both of its z neighbours)
-    for (int p = z0 - 2; p <= z1 + 1; ++p) {
-        sweep::load(A, S, X0, Y0, p, threadIdx.x, blockDim.x);
-        __syncthreads();
-        if (p - 1 >= z0 - 1) sweep::first_colour(A, S, X0, Y0, p - 1, z0, z1, threadIdx.x, blockDim.x);
-        __syncthreads();
-        if (p - 2 >= z0) sweep::second_colour(A, S, X0, Y0, p - 2, threadIdx.x, blockDim.x);
-        __syncthreads();
+    const long long nit = sweep::items(A.d, A.zc);
+    for (long long it = blockIdx.x; it < nit; it += gridDim.x) {
+        int X0, Y0, z0, z1;
+        sweep::item_origin(A.d, A.zc, it, X0, Y0, z0, z1);
+        // plane p is staged, the first colour computed one plane behind it and the second colour
+        // two planes behind (it needs the first colour on both of its z neighbours); the loads of
+        // plane p + 1 are in flight while plane p's colours are computed
+        sweep::Fetch<T> F;
+        sweep::fetch(A, X0, Y0, z0 - 2, threadIdx.x, F);
+        for (int p = z0 - 2; p <= z1 + 1; ++p) {
+            sweep::stage(S, p, threadIdx.x, F);
+            if (p < z1 + 1) sweep::fetch(A, X0, Y0, p + 1, threadIdx.x, F);
+            __syncthreads();
+            if (p - 1 >= z0 - 1) sweep::first_colour(A, S, X0, Y0, p - 1, z0, z1, threadIdx.x, blockDim.x);
+            __syncthreads();
+            if (p - 2 >= z0) sweep::second_colour(A, S, X0, Y0, p - 2, threadIdx.x, blockDim.x);
+            __syncthreads();
+        }
     }
 }
 
@@ -677,6 +684,15 @@ int sm_count() {
 
 template <class T>
 void launch_rbgs_sweep(const Level<T>& L, int first, bool zero_guess, const Level<T>* coarse, cudaStream_t s) {
+    // resident CTAs per SM of the sweep kernel (shared memory bound), found once per precision
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaFuncSetAttribute(k_rbgs_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(sweep::Tile<T>));
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbgs_sweep<T>, sweep::kThreads,
+                                                          sizeof(sweep::Tile<T>)) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+    }
     sweep::Args<T> A;
     A.d = geo_of(L.d);
     A.diag = L.diag;
@@ -688,16 +704,12 @@ void launch_rbgs_sweep(const Level<T>& L, int first, bool zero_guess, const Leve
     A.xout = L.xt;
     A.first = first;
     A.zero_guess = zero_guess ? 1 : 0;
-    A.zc = sweep::chunk_planes(A.d, sm_count());
+    const long long slots = (long long)sm_count() * per_sm;
+    A.zc = sweep::chunk_planes(A.d, slots);
     A.xc = coarse ? coarse->x : nullptr;
     A.cd = coarse ? geo_of(coarse->d) : A.d;
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_rbgs_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(sweep::Tile<T>));
-        configured = true;
-    }
-    const dim3 grid((L.d.nx + sweep::TX - 1) / sweep::TX, (L.d.ny + sweep::TY - 1) / sweep::TY,
-                    (L.d.nz + A.zc - 1) / A.zc);
+    const long long nit = sweep::items(A.d, A.zc);
+    const int grid = (int)(nit < slots ? nit : slots);
     k_rbgs_sweep<T><<<grid, sweep::kThreads, sizeof(sweep::Tile<T>), s>>>(A);
 }
 template <class T>

@@ -6,15 +6,17 @@
 // from the new values of the first.  The first colour's old values are never read, so the sweep
 // is a function of the old second-colour values alone.
 //
-// Layout of the work: a CTA owns a TX x TY column of cells and marches through a chunk of z
-// planes.  Per plane it stages, in shared memory, the old iterate and the five coefficient
-// arrays over the column plus a two-cell halo in x and y, computes the first colour on the
-// column plus a one-cell halo (the halo values are recomputed locally instead of being read from
-// the neighbouring CTA), and one plane behind that the second colour on the column.  The old
-// iterate is read from one buffer and the result written to another, so the sweep is exactly
-// the red-black Gauss-Seidel sweep and does not depend on the order in which CTAs run.  Every
-// array is read once per sweep (plus the halo, mostly from L2) and x is written once: the
-// 7 words per cell of a sweep.
+// Layout of the work: a work item is a TX x TY column of cells over a chunk of z planes; a CTA
+// takes items in turn and marches through the chunk plane by plane.  Per plane it stages, in
+// shared memory, the old iterate and the five coefficient arrays over the column plus a two-cell
+// halo in x and y, computes the first colour on the column plus a one-cell halo (the halo values
+// are recomputed locally instead of being read from the neighbouring CTA) and stores it in place
+// of the old values of those cells, and one plane behind that computes the second colour on the
+// column.  The loads of the next plane are issued into registers before the compute phases of
+// the current one, so their latency overlaps the arithmetic.  The old iterate is read from one
+// buffer and the result written to another, so the sweep is exactly the red-black Gauss-Seidel
+// sweep and does not depend on the order in which CTAs run.  Every array is read once per sweep
+// (plus the halo, mostly from L2) and x is written once: the 7 words per cell of a sweep.
 //
 // Optionally the old iterate is the fine level's x plus the trilinear prolongation of a coarse
 // correction (the V-cycle's coarse-grid correction fused into the first post-smoothing sweep).
@@ -35,11 +37,14 @@
 
 namespace sweep {
 
-constexpr int TX = 32, TY = 16, HALO = 2;
+constexpr int TX = 32, TY = 8, HALO = 2;
 constexpr int PX = TX + 2 * HALO, PY = TY + 2 * HALO;   // staged plane: column plus halo
 constexpr int PLANE = PX * PY;
-constexpr int XR = 3, RR = 3, CR = 4;                   // ring depths: old x, first colour, coefficients
 constexpr int kThreads = 256;
+constexpr int PER_THREAD = (PLANE + kThreads - 1) / kThreads;   // staged positions per thread
+// ring depths, in planes: x holds p-3..p (the second colour of p-2 reads the first colour of
+// p-3..p-1), b/diag/wx/wy hold p-2..p, wz holds p-3..p (the -z face of plane p-2)
+constexpr int XR = 4, CR = 3, ZR = 4;
 
 struct Geo {
     int nx, ny, nz;
@@ -58,7 +63,7 @@ struct Args {
     T* xout;           // new iterate (must not alias xin)
     int first;         // colour updated first
     int zero_guess;    // old iterate = 0
-    int zc;            // z planes per CTA chunk
+    int zc;            // z planes per work item
     // fused coarse-grid correction: old iterate = xin + P xc (xc null: none)
     const T* xc;
     Geo cd;
@@ -66,24 +71,34 @@ struct Args {
 
 template <class T>
 struct Tile {
-    T xo[XR][PLANE];   // old iterate
-    T rd[RR][PLANE];   // first-colour values
-    T cb[CR][PLANE];   // b
-    T cg[CR][PLANE];   // diag
-    T cx[CR][PLANE];   // wx
-    T cy[CR][PLANE];   // wy
-    T cz[CR][PLANE];   // wz
+    T x[XR][PLANE];    // old iterate; first-colour cells overwritten with their new values
+    T b[CR][PLANE];
+    T dg[CR][PLANE];
+    T wx[CR][PLANE];
+    T wy[CR][PLANE];
+    T wz[ZR][PLANE];
+};
+
+// one thread's share of a staged plane, held in registers between its load and its store
+template <class T>
+struct Fetch {
+    T x[PER_THREAD], b[PER_THREAD], dg[PER_THREAD], wx[PER_THREAD], wy[PER_THREAD], wz[PER_THREAD];
 };
 
 RT_HD int ring(int p, int n) { return ((p % n) + n) % n; }
 
-// global coordinate along an axis for local coordinate c of a tile starting at c0: the wrapped
-// index, or -1 outside a non-periodic axis
+// global coordinate along an axis: the wrapped index, or -1 outside a non-periodic axis
 RT_HD int gcoord(int c, int n, int per) {
     if (c >= 0 && c < n) return c;
     if (!per) return -1;
     return ((c % n) + n) % n;
 }
+
+// number of work items and their layout: columns of TX x TY cells times chunks of zc planes
+RT_HD int columns_x(const Geo& d) { return (d.nx + TX - 1) / TX; }
+RT_HD int columns_y(const Geo& d) { return (d.ny + TY - 1) / TY; }
+RT_HD int chunks(const Geo& d, int zc) { return (d.nz + zc - 1) / zc; }
+RT_HD long long items(const Geo& d, int zc) { return (long long)columns_x(d) * columns_y(d) * chunks(d, zc); }
 
 // coarse cell value of the trilinear cell-centred prolongation at fine cell (x, y, z)
 template <class T>
@@ -111,37 +126,58 @@ RT_HD T prolong_at(const Args<T>& A, int x, int y, int z) {
     return w1 * v1 + w2 * v2;
 }
 
-// stage plane p (old iterate and coefficients over the column plus halo)
+// load this thread's share of plane p (old iterate and coefficients over the column plus halo)
 template <class T>
-RT_HD void load(const Args<T>& A, Tile<T>& S, int X0, int Y0, int p, int tid, int nth) {
+RT_HD void fetch(const Args<T>& A, int X0, int Y0, int p, int tid, Fetch<T>& F) {
     const Geo& d = A.d;
     const int gz = gcoord(p, d.nz, d.per[2]);
-    const int xs = ring(p, XR), cs = ring(p, CR);
     const long long sy = d.nx, sz = (long long)d.nx * d.ny;
-    for (int k = tid; k < PLANE; k += nth) {
-        const int lx = k % PX - HALO, ly = k / PX - HALO;
-        const int gx = gcoord(X0 + lx, d.nx, d.per[0]);
-        const int gy = gcoord(Y0 + ly, d.ny, d.per[1]);
+#pragma unroll
+    for (int j = 0; j < PER_THREAD; ++j) {
+        const int k = tid + j * kThreads;
         T xo = T(0), b = T(0), dg = T(0), wx = T(0), wy = T(0), wz = T(0);
-        if (gx >= 0 && gy >= 0 && gz >= 0) {
-            const long long i = (long long)gz * sz + (long long)gy * sy + gx;
-            RT_SWEEP_CHECK(i >= 0 && i < sz * d.nz);
-            b = A.b[i];
-            dg = A.diag[i];
-            wx = A.wx[i];
-            wy = A.wy[i];
-            wz = A.wz[i];
-            if (!A.zero_guess) {
-                xo = A.xin[i];
-                if (A.xc) xo += prolong_at(A, gx, gy, gz);
+        if (k < PLANE) {
+            const int lx = k % PX - HALO, ly = k / PX - HALO;
+            const int gx = gcoord(X0 + lx, d.nx, d.per[0]);
+            const int gy = gcoord(Y0 + ly, d.ny, d.per[1]);
+            if (gx >= 0 && gy >= 0 && gz >= 0) {
+                const long long i = (long long)gz * sz + (long long)gy * sy + gx;
+                RT_SWEEP_CHECK(i >= 0 && i < sz * d.nz);
+                b = A.b[i];
+                dg = A.diag[i];
+                wx = A.wx[i];
+                wy = A.wy[i];
+                wz = A.wz[i];
+                if (!A.zero_guess) {
+                    xo = A.xin[i];
+                    if (A.xc) xo += prolong_at(A, gx, gy, gz);
+                }
             }
         }
-        S.xo[xs][k] = xo;
-        S.cb[cs][k] = b;
-        S.cg[cs][k] = dg;
-        S.cx[cs][k] = wx;
-        S.cy[cs][k] = wy;
-        S.cz[cs][k] = wz;
+        F.x[j] = xo;
+        F.b[j] = b;
+        F.dg[j] = dg;
+        F.wx[j] = wx;
+        F.wy[j] = wy;
+        F.wz[j] = wz;
+    }
+}
+
+// store this thread's share of plane p into the rings
+template <class T>
+RT_HD void stage(Tile<T>& S, int p, int tid, const Fetch<T>& F) {
+    const int xs = ring(p, XR), cs = ring(p, CR), zs = ring(p, ZR);
+#pragma unroll
+    for (int j = 0; j < PER_THREAD; ++j) {
+        const int k = tid + j * kThreads;
+        if (k < PLANE) {
+            S.x[xs][k] = F.x[j];
+            S.b[cs][k] = F.b[j];
+            S.dg[cs][k] = F.dg[j];
+            S.wx[cs][k] = F.wx[j];
+            S.wy[cs][k] = F.wy[j];
+            S.wz[zs][k] = F.wz[j];
+        }
     }
 }
 
@@ -154,67 +190,73 @@ RT_HD int colour(const Geo& d, int X0, int Y0, int lx, int ly, int p) {
     return (gx + gy + gz) & 1;
 }
 
-// first colour on plane q over the column plus a one-cell halo; its column cells of planes
-// z0 <= q < z1 are written out
+// first colour on plane q over the column plus a one-cell halo, stored in place of the old
+// values of those cells (their old values are never read); the column cells of planes
+// z0 <= q < z1 are also written out
 template <class T>
 RT_HD void first_colour(const Args<T>& A, Tile<T>& S, int X0, int Y0, int q, int z0, int z1, int tid, int nth) {
     const Geo& d = A.d;
-    const int rs = ring(q, RR), cs = ring(q, CR), cm = ring(q - 1, CR);
+    const int cs = ring(q, CR), zs = ring(q, ZR), zm = ring(q - 1, ZR);
     const int xs = ring(q, XR), xm = ring(q - 1, XR), xp = ring(q + 1, XR);
     const long long sy = d.nx, sz = (long long)d.nx * d.ny;
     constexpr int W1 = TX + 2, H1 = TY + 2;
     for (int k = tid; k < W1 * H1; k += nth) {
         const int lx = k % W1 - 1, ly = k / W1 - 1;
+        if (colour(d, X0, Y0, lx, ly, q) != A.first) continue;
         const int c = (ly + HALO) * PX + (lx + HALO);
-        T v = T(0);
-        if (colour(d, X0, Y0, lx, ly, q) == A.first) {
-            T num = S.cb[cs][c];
-            if (!A.zero_guess) {
-                num += S.cx[cs][c] * S.xo[xs][c + 1] + S.cx[cs][c - 1] * S.xo[xs][c - 1] +
-                       S.cy[cs][c] * S.xo[xs][c + PX] + S.cy[cs][c - PX] * S.xo[xs][c - PX] +
-                       S.cz[cs][c] * S.xo[xp][c] + S.cz[cm][c] * S.xo[xm][c];
-            }
-            v = num / S.cg[cs][c];
-            if (q >= z0 && q < z1 && lx >= 0 && lx < TX && ly >= 0 && ly < TY && X0 + lx < d.nx &&
-                Y0 + ly < d.ny) {
-                const long long i = (long long)q * sz + (long long)(Y0 + ly) * sy + (X0 + lx);
-                RT_SWEEP_CHECK(i >= 0 && i < sz * d.nz);
-                A.xout[i] = v;
-            }
+        T num = S.b[cs][c];
+        if (!A.zero_guess) {
+            num += S.wx[cs][c] * S.x[xs][c + 1] + S.wx[cs][c - 1] * S.x[xs][c - 1] +
+                   S.wy[cs][c] * S.x[xs][c + PX] + S.wy[cs][c - PX] * S.x[xs][c - PX] +
+                   S.wz[zs][c] * S.x[xp][c] + S.wz[zm][c] * S.x[xm][c];
         }
-        S.rd[rs][c] = v;
+        const T v = num / S.dg[cs][c];
+        S.x[xs][c] = v;
+        if (q >= z0 && q < z1 && lx >= 0 && lx < TX && ly >= 0 && ly < TY && X0 + lx < d.nx && Y0 + ly < d.ny) {
+            const long long i = (long long)q * sz + (long long)(Y0 + ly) * sy + (X0 + lx);
+            RT_SWEEP_CHECK(i >= 0 && i < sz * d.nz);
+            A.xout[i] = v;
+        }
     }
 }
 
 // second colour on plane q (z0 <= q < z1) over the column, from the first colour's new values
 template <class T>
-RT_HD void second_colour(const Args<T>& A, Tile<T>& S, int X0, int Y0, int q, int tid, int nth) {
+RT_HD void second_colour(const Args<T>& A, const Tile<T>& S, int X0, int Y0, int q, int tid, int nth) {
     const Geo& d = A.d;
-    const int rs = ring(q, RR), rm = ring(q - 1, RR), rp = ring(q + 1, RR);
-    const int cs = ring(q, CR), cm = ring(q - 1, CR);
+    const int xs = ring(q, XR), xm = ring(q - 1, XR), xp = ring(q + 1, XR);
+    const int cs = ring(q, CR), zs = ring(q, ZR), zm = ring(q - 1, ZR);
     const long long sy = d.nx, sz = (long long)d.nx * d.ny;
     for (int k = tid; k < TX * TY; k += nth) {
         const int lx = k % TX, ly = k / TX;
         if (X0 + lx >= d.nx || Y0 + ly >= d.ny) continue;
         if (colour(d, X0, Y0, lx, ly, q) != 1 - A.first) continue;
         const int c = (ly + HALO) * PX + (lx + HALO);
-        const T num = S.cb[cs][c] + S.cx[cs][c] * S.rd[rs][c + 1] + S.cx[cs][c - 1] * S.rd[rs][c - 1] +
-                      S.cy[cs][c] * S.rd[rs][c + PX] + S.cy[cs][c - PX] * S.rd[rs][c - PX] +
-                      S.cz[cs][c] * S.rd[rp][c] + S.cz[cm][c] * S.rd[rm][c];
+        const T num = S.b[cs][c] + S.wx[cs][c] * S.x[xs][c + 1] + S.wx[cs][c - 1] * S.x[xs][c - 1] +
+                      S.wy[cs][c] * S.x[xs][c + PX] + S.wy[cs][c - PX] * S.x[xs][c - PX] +
+                      S.wz[zs][c] * S.x[xp][c] + S.wz[zm][c] * S.x[xm][c];
         const long long i = (long long)q * sz + (long long)(Y0 + ly) * sy + (X0 + lx);
         RT_SWEEP_CHECK(i >= 0 && i < sz * d.nz);
-        A.xout[i] = num / S.cg[cs][c];
+        A.xout[i] = num / S.dg[cs][c];
     }
 }
 
-// z planes per chunk for a level: enough CTAs to cover the SMs about four times over, chunks of
-// at least four planes
-inline int chunk_planes(const Geo& d, int nsm) {
-    const long long cols = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY);
-    long long chunks = (4LL * nsm + cols - 1) / cols;
-    if (chunks < 1) chunks = 1;
-    int zc = (int)((d.nz + chunks - 1) / chunks);
-    if (zc < 4) zc = 4;
+// origin and z range of work item `it`
+RT_HD void item_origin(const Geo& d, int zc, long long it, int& X0, int& Y0, int& z0, int& z1) {
+    const int cx = columns_x(d), cy = columns_y(d);
+    const long long col = it % ((long long)cx * cy);
+    const int ch = (int)(it / ((long long)cx * cy));
+    X0 = (int)(col % cx) * TX;
+    Y0 = (int)(col / cx) * TY;
+    z0 = ch * zc;
+    z1 = z0 + zc < d.nz ? z0 + zc : d.nz;
+}
+
+// z planes per work item: 16, halved (to no fewer than 4) while the items would not fill
+// `slots` resident CTAs
+inline int chunk_planes(const Geo& d, long long slots) {
+    int zc = 16;
+    while (zc > 4 && items(d, zc) < slots) zc /= 2;
     if (zc > d.nz) zc = d.nz;
     return zc;
 }

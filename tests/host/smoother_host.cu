@@ -21,7 +21,7 @@ static long long g_bad_index = 0;
 template <class T>
 static long long run_sweep(int nx, int ny, int nz, const int* per, const T* diag, const T* wx, const T* wy, const T* wz,
                            const T* b, const T* xin, T* xout, int first, int zero, int zc, const T* xc, int cnx,
-                           int cny, int cnz, int nth) {
+                           int cny, int cnz, int nth, int grid) {
     g_bad_index = 0;
     sweep::Args<T> A;
     A.d.nx = nx;
@@ -37,7 +37,8 @@ static long long run_sweep(int nx, int ny, int nz, const int* per, const T* diag
     A.xout = xout;
     A.first = first;
     A.zero_guess = zero;
-    A.zc = zc > 0 ? zc : sweep::chunk_planes(A.d, 152);
+    A.zc = zc > 0 ? zc : sweep::chunk_planes(A.d, 152 * 6);
+    if (grid <= 0) grid = 1;
     A.xc = xc;
     A.cd.nx = cnx;
     A.cd.ny = cny;
@@ -47,42 +48,48 @@ static long long run_sweep(int nx, int ny, int nz, const int* per, const T* diag
     sweep::Tile<T>& S = tile[0];
     T* raw = reinterpret_cast<T*>(&S);
     const size_t nraw = sizeof(S) / sizeof(T);
-    const int gx = (nx + sweep::TX - 1) / sweep::TX, gy = (ny + sweep::TY - 1) / sweep::TY;
-    const int gz = (nz + A.zc - 1) / A.zc;
-    for (int bz = 0; bz < gz; ++bz)
-        for (int by = 0; by < gy; ++by)
-            for (int bx = 0; bx < gx; ++bx) {
-                for (size_t k = 0; k < nraw; ++k) raw[k] = std::numeric_limits<T>::quiet_NaN();
-                const int X0 = bx * sweep::TX, Y0 = by * sweep::TY;
-                const int z0 = bz * A.zc, z1 = z0 + A.zc < nz ? z0 + A.zc : nz;
-                for (int p = z0 - 2; p <= z1 + 1; ++p) {
-                    for (int t = 0; t < nth; ++t) sweep::load(A, S, X0, Y0, p, t, nth);
-                    if (p - 1 >= z0 - 1)
-                        for (int t = 0; t < nth; ++t) sweep::first_colour(A, S, X0, Y0, p - 1, z0, z1, t, nth);
-                    if (p - 2 >= z0)
-                        for (int t = 0; t < nth; ++t) sweep::second_colour(A, S, X0, Y0, p - 2, t, nth);
-                }
+    std::vector<sweep::Fetch<T>> F(sweep::kThreads);
+    const long long nit = sweep::items(A.d, A.zc);
+    // the CTAs of a launch with `grid` blocks, each taking items blockIdx, blockIdx + grid, ...
+    for (int blk = 0; blk < grid; ++blk)
+        for (long long it = blk; it < nit; it += grid) {
+            for (size_t k = 0; k < nraw; ++k) raw[k] = std::numeric_limits<T>::quiet_NaN();
+            int X0, Y0, z0, z1;
+            sweep::item_origin(A.d, A.zc, it, X0, Y0, z0, z1);
+            for (int t = 0; t < sweep::kThreads; ++t) sweep::fetch(A, X0, Y0, z0 - 2, t, F[t]);
+            for (int p = z0 - 2; p <= z1 + 1; ++p) {
+                for (int t = 0; t < sweep::kThreads; ++t) sweep::stage(S, p, t, F[t]);
+                if (p < z1 + 1)
+                    for (int t = 0; t < sweep::kThreads; ++t) sweep::fetch(A, X0, Y0, p + 1, t, F[t]);
+                if (p - 1 >= z0 - 1)
+                    for (int t = 0; t < nth; ++t) sweep::first_colour(A, S, X0, Y0, p - 1, z0, z1, t, nth);
+                if (p - 2 >= z0)
+                    for (int t = 0; t < nth; ++t) sweep::second_colour(A, S, X0, Y0, p - 2, t, nth);
             }
+        }
     return g_bad_index;
 }
 
 extern "C" {
 long long sweep_host_f64(int nx, int ny, int nz, const int* per, const double* diag, const double* wx,
                          const double* wy, const double* wz, const double* b, const double* xin, double* xout,
-                         int first, int zero, int zc, const double* xc, int cnx, int cny, int cnz, int nth) {
-    return run_sweep<double>(nx, ny, nz, per, diag, wx, wy, wz, b, xin, xout, first, zero, zc, xc, cnx, cny, cnz, nth);
+                         int first, int zero, int zc, const double* xc, int cnx, int cny, int cnz, int nth,
+                         int grid) {
+    return run_sweep<double>(nx, ny, nz, per, diag, wx, wy, wz, b, xin, xout, first, zero, zc, xc, cnx, cny, cnz, nth,
+                             grid);
 }
 long long sweep_host_f32(int nx, int ny, int nz, const int* per, const float* diag, const float* wx, const float* wy,
                          const float* wz, const float* b, const float* xin, float* xout, int first, int zero, int zc,
-                         const float* xc, int cnx, int cny, int cnz, int nth) {
-    return run_sweep<float>(nx, ny, nz, per, diag, wx, wy, wz, b, xin, xout, first, zero, zc, xc, cnx, cny, cnz, nth);
+                         const float* xc, int cnx, int cny, int cnz, int nth, int grid) {
+    return run_sweep<float>(nx, ny, nz, per, diag, wx, wy, wz, b, xin, xout, first, zero, zc, xc, cnx, cny, cnz, nth,
+                            grid);
 }
-int sweep_chunk_planes(int nx, int ny, int nz, int nsm) {
+int sweep_chunk_planes(int nx, int ny, int nz, long long slots) {
     sweep::Geo d;
     d.nx = nx;
     d.ny = ny;
     d.nz = nz;
     d.per[0] = d.per[1] = d.per[2] = 0;
-    return sweep::chunk_planes(d, nsm);
+    return sweep::chunk_planes(d, slots);
 }
 }

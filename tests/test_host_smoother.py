@@ -87,7 +87,7 @@ def _prolong_reference(xc, fshape, per):
     return out
 
 
-def _call(lib, dtype, shape, per, diag, w, b, xin, first, zero, zc, xc=None, nth=256):
+def _call(lib, dtype, shape, per, diag, w, b, xin, first, zero, zc, xc=None, nth=256, grid=7):
     nz, ny, nx = shape
     fn = lib.sweep_host_f64 if dtype == np.float64 else lib.sweep_host_f32
     fn.restype = ctypes.c_longlong
@@ -98,7 +98,7 @@ def _call(lib, dtype, shape, per, diag, w, b, xin, first, zero, zc, xc=None, nth
     cshape = xc.shape if xc is not None else (1, 1, 1)
     xcp = arr(xc).ctypes.data_as(ctypes.c_void_p) if xc is not None else None
     bad = fn(nx, ny, nz, perc, *[a.ctypes.data_as(ctypes.c_void_p) for a in args], out.ctypes.data_as(ctypes.c_void_p),
-             first, zero, zc, xcp, cshape[2], cshape[1], cshape[0], nth)
+             first, zero, zc, xcp, cshape[2], cshape[1], cshape[0], nth, grid)
     return out, bad
 
 
@@ -117,7 +117,7 @@ def test_fused_sweep_equals_red_black_gauss_seidel(lib, shape, per, zc, dtype):
     tol = 1e-13 if dtype == np.float64 else 2e-6
     for first in (0, 1):
         ref = _rbgs_reference(diag, w, b, x0, first)
-        got, bad = _call(lib, dtype, shape, per, diag, w, b, x0, first, 0, zc)
+        got, bad = _call(lib, dtype, shape, per, diag, w, b, x0, first, 0, zc, grid=1 if first else 7)
         assert bad == 0
         np.testing.assert_allclose(got, ref, rtol=tol, atol=tol * np.abs(ref).max())
     ref0 = _rbgs_reference(diag, w, b, np.zeros(shape), 0)
@@ -141,10 +141,10 @@ def test_fused_sweep_with_coarse_correction(lib, shape, per, zc):
     np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
 
 
-def test_chunking_covers_the_sms(lib):
-    """Enough CTAs to cover the SMs four times over (256^3: 8 x 16 columns, 5 chunks of 52
-    planes, 640 CTAs); small levels keep chunks of at least 4 planes."""
-    zc = lib.sweep_chunk_planes(256, 256, 256, 152)
-    assert zc == 52 and 8 * 16 * -(-256 // zc) >= 4 * 152
-    assert lib.sweep_chunk_planes(8, 8, 8, 152) == 4
-    assert lib.sweep_chunk_planes(16, 16, 2, 152) == 2
+def test_chunking_fills_the_resident_ctas(lib):
+    """Work items of 16 planes while they fill the resident CTAs (256^3: 8 x 32 columns, 16 chunks,
+    4096 items), halved down to 4 planes for small levels."""
+    lib.sweep_chunk_planes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong]
+    assert lib.sweep_chunk_planes(256, 256, 256, 912) == 16
+    assert lib.sweep_chunk_planes(64, 64, 64, 912) == 4
+    assert lib.sweep_chunk_planes(16, 16, 2, 912) == 2
