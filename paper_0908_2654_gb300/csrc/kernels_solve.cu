@@ -256,20 +256,20 @@ __global__ void __launch_bounds__(sweep::kThreads) k_rbgs_sweep(sweep::Args<T> A
     sweep::Tile<T>& S = *reinterpret_cast<sweep::Tile<T>*>(smem_sweep);
     const long long nit = sweep::items(A.d, A.zc);
     for (long long it = blockIdx.x; it < nit; it += gridDim.x) {
-        int X0, Y0, z0, z1;
-        sweep::item_origin(A.d, A.zc, it, X0, Y0, z0, z1);
+        sweep::Item I;
+        sweep::item_setup(A, it, threadIdx.x, I);
         // plane p is staged, the first colour computed one plane behind it and the second colour
         // two planes behind (it needs the first colour on both of its z neighbours); the loads of
         // plane p + 1 are in flight while plane p's colours are computed
         sweep::Fetch<T> F;
-        sweep::fetch(A, X0, Y0, z0 - 2, threadIdx.x, F);
-        for (int p = z0 - 2; p <= z1 + 1; ++p) {
+        sweep::fetch(A, I, I.z0 - 2, F);
+        for (int p = I.z0 - 2; p <= I.z1 + 1; ++p) {
             sweep::stage(S, p, threadIdx.x, F);
-            if (p < z1 + 1) sweep::fetch(A, X0, Y0, p + 1, threadIdx.x, F);
+            if (p < I.z1 + 1) sweep::fetch(A, I, p + 1, F);
             __syncthreads();
-            if (p - 1 >= z0 - 1) sweep::first_colour(A, S, X0, Y0, p - 1, z0, z1, threadIdx.x, blockDim.x);
+            if (p - 1 >= I.z0 - 1) sweep::first_colour(A, S, I, p - 1);
             __syncthreads();
-            if (p - 2 >= z0) sweep::second_colour(A, S, X0, Y0, p - 2, threadIdx.x, blockDim.x);
+            if (p - 2 >= I.z0) sweep::second_colour(A, S, I, p - 2);
             __syncthreads();
         }
     }

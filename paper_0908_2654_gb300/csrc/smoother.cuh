@@ -126,31 +126,102 @@ RT_HD T prolong_at(const Args<T>& A, int x, int y, int z) {
     return w1 * v1 + w2 * v2;
 }
 
-// load this thread's share of plane p (old iterate and coefficients over the column plus halo)
+// Per-thread addressing of a work item, fixed for all its planes: the in-plane offsets of the
+// thread's staged positions (-1 outside a non-periodic edge) and of its first- and second-colour
+// pairs.  A pair is two x-neighbours starting at an odd (first colour, column plus halo) or even
+// (second colour, column) local x; exactly one of them has each colour, so every thread of a
+// colour phase updates one cell and no lane waits on a colour test.
+constexpr int P1 = (TX + 2) / 2 * (TY + 2);   // first-colour pairs: 17 x 10 for 32 x 8
+constexpr int P2 = TX / 2 * TY;               // second-colour pairs: 16 x 8
+static_assert(P1 <= kThreads && P2 <= kThreads, "one pair per thread");
+
+struct Item {
+    int X0, Y0, z0, z1;
+    int off[PER_THREAD];         // staged position: gy * nx + gx, or -1 (a plane holds < 2^31 cells)
+    // first-colour pair: shared-memory index of its left cell, whether each cell lies in the grid,
+    // the left cell's parity (gx + gy) & 1, whether each is a column cell to write out, and the
+    // left cell's in-plane offset
+    int c1;
+    bool in1[2];
+    int par1;
+    bool w1[2];
+    int o1;
+    // second-colour pair (always column cells)
+    int c2;
+    bool in2[2];
+    int par2;
+    int o2;
+};
+
 template <class T>
-RT_HD void fetch(const Args<T>& A, int X0, int Y0, int p, int tid, Fetch<T>& F) {
+RT_HD void item_setup(const Args<T>& A, long long it, int tid, Item& I) {
     const Geo& d = A.d;
-    const int gz = gcoord(p, d.nz, d.per[2]);
-    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+    const int cx = columns_x(d), cy = columns_y(d);
+    const long long col = it % ((long long)cx * cy);
+    const int ch = (int)(it / ((long long)cx * cy));
+    I.X0 = (int)(col % cx) * TX;
+    I.Y0 = (int)(col / cx) * TY;
+    I.z0 = ch * A.zc;
+    I.z1 = I.z0 + A.zc < d.nz ? I.z0 + A.zc : d.nz;
 #pragma unroll
     for (int j = 0; j < PER_THREAD; ++j) {
         const int k = tid + j * kThreads;
-        T xo = T(0), b = T(0), dg = T(0), wx = T(0), wy = T(0), wz = T(0);
+        I.off[j] = -1;
         if (k < PLANE) {
-            const int lx = k % PX - HALO, ly = k / PX - HALO;
-            const int gx = gcoord(X0 + lx, d.nx, d.per[0]);
-            const int gy = gcoord(Y0 + ly, d.ny, d.per[1]);
-            if (gx >= 0 && gy >= 0 && gz >= 0) {
-                const long long i = (long long)gz * sz + (long long)gy * sy + gx;
-                RT_SWEEP_CHECK(i >= 0 && i < sz * d.nz);
-                b = A.b[i];
-                dg = A.diag[i];
-                wx = A.wx[i];
-                wy = A.wy[i];
-                wz = A.wz[i];
-                if (!A.zero_guess) {
-                    xo = A.xin[i];
-                    if (A.xc) xo += prolong_at(A, gx, gy, gz);
+            const int gx = gcoord(I.X0 + k % PX - HALO, d.nx, d.per[0]);
+            const int gy = gcoord(I.Y0 + k / PX - HALO, d.ny, d.per[1]);
+            if (gx >= 0 && gy >= 0) I.off[j] = gy * d.nx + gx;
+        }
+    }
+    I.c1 = -1;
+    if (tid < P1) {
+        const int lx = -1 + 2 * (tid % ((TX + 2) / 2)), ly = -1 + tid / ((TX + 2) / 2);
+        const int gy = gcoord(I.Y0 + ly, d.ny, d.per[1]);
+        const int g0 = gcoord(I.X0 + lx, d.nx, d.per[0]), g1 = gcoord(I.X0 + lx + 1, d.nx, d.per[0]);
+        I.c1 = (ly + HALO) * PX + (lx + HALO);
+        I.in1[0] = gy >= 0 && g0 >= 0;
+        I.in1[1] = gy >= 0 && g1 >= 0;
+        // parity of the left cell; the right one has the other parity (even dimensions)
+        I.par1 = I.in1[0] ? (g0 + gy) & 1 : (I.in1[1] ? (g1 + gy + 1) & 1 : 0);
+        const bool row = ly >= 0 && ly < TY && I.Y0 + ly < d.ny;
+        I.w1[0] = row && lx >= 0 && I.X0 + lx < d.nx;
+        I.w1[1] = row && lx + 1 < TX && I.X0 + lx + 1 < d.nx;
+        I.o1 = (I.Y0 + ly) * d.nx + (I.X0 + lx);
+    }
+    I.c2 = -1;
+    if (tid < P2) {
+        const int lx = 2 * (tid % (TX / 2)), ly = tid / (TX / 2);
+        I.c2 = (ly + HALO) * PX + (lx + HALO);
+        const bool row = I.Y0 + ly < d.ny;
+        I.in2[0] = row && I.X0 + lx < d.nx;
+        I.in2[1] = row && I.X0 + lx + 1 < d.nx;
+        I.par2 = (I.X0 + lx + I.Y0 + ly) & 1;
+        I.o2 = (I.Y0 + ly) * d.nx + (I.X0 + lx);
+    }
+}
+
+// load this thread's share of plane p (old iterate and coefficients over the column plus halo)
+template <class T>
+RT_HD void fetch(const Args<T>& A, const Item& I, int p, Fetch<T>& F) {
+    const Geo& d = A.d;
+    const int gz = gcoord(p, d.nz, d.per[2]);
+    const long long plane = (long long)gz * d.nx * d.ny;
+#pragma unroll
+    for (int j = 0; j < PER_THREAD; ++j) {
+        T xo = T(0), b = T(0), dg = T(0), wx = T(0), wy = T(0), wz = T(0);
+        if (I.off[j] >= 0 && gz >= 0) {
+            const long long i = plane + I.off[j];
+            RT_SWEEP_CHECK(i >= 0 && i < (long long)d.nx * d.ny * d.nz);
+            b = A.b[i];
+            dg = A.diag[i];
+            wx = A.wx[i];
+            wy = A.wy[i];
+            wz = A.wz[i];
+            if (!A.zero_guess) {
+                xo = A.xin[i];
+                if (A.xc) {
+                    const int r = I.off[j] / d.nx;
+                    xo += prolong_at(A, I.off[j] - r * d.nx, r, gz);
                 }
             }
         }
@@ -181,75 +252,54 @@ RT_HD void stage(Tile<T>& S, int p, int tid, const Fetch<T>& F) {
     }
 }
 
-// colour of the cell at local (lx, ly) on plane p, or -1 when it lies outside the grid
-RT_HD int colour(const Geo& d, int X0, int Y0, int lx, int ly, int p) {
-    const int gx = gcoord(X0 + lx, d.nx, d.per[0]);
-    const int gy = gcoord(Y0 + ly, d.ny, d.per[1]);
-    const int gz = gcoord(p, d.nz, d.per[2]);
-    if (gx < 0 || gy < 0 || gz < 0) return -1;
-    return (gx + gy + gz) & 1;
+// (b + sum_faces w x_nb) / diag at shared-memory index c of a plane: coefficients from slots
+// (cs, zs; zm for the -z face), x from slots (xs; xm, xp for the z neighbours)
+template <class T>
+RT_HD T update(const Tile<T>& S, int c, int cs, int zs, int zm, int xs, int xm, int xp, bool zero) {
+    T num = S.b[cs][c];
+    if (!zero) {
+        num += S.wx[cs][c] * S.x[xs][c + 1] + S.wx[cs][c - 1] * S.x[xs][c - 1] + S.wy[cs][c] * S.x[xs][c + PX] +
+               S.wy[cs][c - PX] * S.x[xs][c - PX] + S.wz[zs][c] * S.x[xp][c] + S.wz[zm][c] * S.x[xm][c];
+    }
+    return num / S.dg[cs][c];
 }
 
 // first colour on plane q over the column plus a one-cell halo, stored in place of the old
 // values of those cells (their old values are never read); the column cells of planes
 // z0 <= q < z1 are also written out
 template <class T>
-RT_HD void first_colour(const Args<T>& A, Tile<T>& S, int X0, int Y0, int q, int z0, int z1, int tid, int nth) {
+RT_HD void first_colour(const Args<T>& A, Tile<T>& S, const Item& I, int q) {
+    if (I.c1 < 0) return;
     const Geo& d = A.d;
-    const int cs = ring(q, CR), zs = ring(q, ZR), zm = ring(q - 1, ZR);
-    const int xs = ring(q, XR), xm = ring(q - 1, XR), xp = ring(q + 1, XR);
-    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
-    constexpr int W1 = TX + 2, H1 = TY + 2;
-    for (int k = tid; k < W1 * H1; k += nth) {
-        const int lx = k % W1 - 1, ly = k / W1 - 1;
-        if (colour(d, X0, Y0, lx, ly, q) != A.first) continue;
-        const int c = (ly + HALO) * PX + (lx + HALO);
-        T num = S.b[cs][c];
-        if (!A.zero_guess) {
-            num += S.wx[cs][c] * S.x[xs][c + 1] + S.wx[cs][c - 1] * S.x[xs][c - 1] +
-                   S.wy[cs][c] * S.x[xs][c + PX] + S.wy[cs][c - PX] * S.x[xs][c - PX] +
-                   S.wz[zs][c] * S.x[xp][c] + S.wz[zm][c] * S.x[xm][c];
-        }
-        const T v = num / S.dg[cs][c];
-        S.x[xs][c] = v;
-        if (q >= z0 && q < z1 && lx >= 0 && lx < TX && ly >= 0 && ly < TY && X0 + lx < d.nx && Y0 + ly < d.ny) {
-            const long long i = (long long)q * sz + (long long)(Y0 + ly) * sy + (X0 + lx);
-            RT_SWEEP_CHECK(i >= 0 && i < sz * d.nz);
-            A.xout[i] = v;
-        }
+    const int gz = gcoord(q, d.nz, d.per[2]);
+    if (gz < 0) return;
+    // the pair's cell of the first colour: the left one when its parity matches
+    const int o = ((I.par1 + gz) & 1) == A.first ? 0 : 1;
+    if (!I.in1[o]) return;
+    const int c = I.c1 + o;
+    const T v = update(S, c, ring(q, CR), ring(q, ZR), ring(q - 1, ZR), ring(q, XR), ring(q - 1, XR), ring(q + 1, XR),
+                       A.zero_guess != 0);
+    S.x[ring(q, XR)][c] = v;
+    if (I.w1[o] && q >= I.z0 && q < I.z1) {
+        const long long i = (long long)q * d.nx * d.ny + I.o1 + o;
+        RT_SWEEP_CHECK(i >= 0 && i < (long long)d.nx * d.ny * d.nz);
+        A.xout[i] = v;
     }
 }
 
 // second colour on plane q (z0 <= q < z1) over the column, from the first colour's new values
 template <class T>
-RT_HD void second_colour(const Args<T>& A, const Tile<T>& S, int X0, int Y0, int q, int tid, int nth) {
+RT_HD void second_colour(const Args<T>& A, const Tile<T>& S, const Item& I, int q) {
+    if (I.c2 < 0) return;
     const Geo& d = A.d;
-    const int xs = ring(q, XR), xm = ring(q - 1, XR), xp = ring(q + 1, XR);
-    const int cs = ring(q, CR), zs = ring(q, ZR), zm = ring(q - 1, ZR);
-    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
-    for (int k = tid; k < TX * TY; k += nth) {
-        const int lx = k % TX, ly = k / TX;
-        if (X0 + lx >= d.nx || Y0 + ly >= d.ny) continue;
-        if (colour(d, X0, Y0, lx, ly, q) != 1 - A.first) continue;
-        const int c = (ly + HALO) * PX + (lx + HALO);
-        const T num = S.b[cs][c] + S.wx[cs][c] * S.x[xs][c + 1] + S.wx[cs][c - 1] * S.x[xs][c - 1] +
-                      S.wy[cs][c] * S.x[xs][c + PX] + S.wy[cs][c - PX] * S.x[xs][c - PX] +
-                      S.wz[zs][c] * S.x[xp][c] + S.wz[zm][c] * S.x[xm][c];
-        const long long i = (long long)q * sz + (long long)(Y0 + ly) * sy + (X0 + lx);
-        RT_SWEEP_CHECK(i >= 0 && i < sz * d.nz);
-        A.xout[i] = num / S.dg[cs][c];
-    }
-}
-
-// origin and z range of work item `it`
-RT_HD void item_origin(const Geo& d, int zc, long long it, int& X0, int& Y0, int& z0, int& z1) {
-    const int cx = columns_x(d), cy = columns_y(d);
-    const long long col = it % ((long long)cx * cy);
-    const int ch = (int)(it / ((long long)cx * cy));
-    X0 = (int)(col % cx) * TX;
-    Y0 = (int)(col / cx) * TY;
-    z0 = ch * zc;
-    z1 = z0 + zc < d.nz ? z0 + zc : d.nz;
+    const int o = ((I.par2 + q) & 1) == 1 - A.first ? 0 : 1;
+    if (!I.in2[o]) return;
+    const int c = I.c2 + o;
+    const T v = update(S, c, ring(q, CR), ring(q, ZR), ring(q - 1, ZR), ring(q, XR), ring(q - 1, XR), ring(q + 1, XR),
+                       false);
+    const long long i = (long long)q * d.nx * d.ny + I.o2 + o;
+    RT_SWEEP_CHECK(i >= 0 && i < (long long)d.nx * d.ny * d.nz);
+    A.xout[i] = v;
 }
 
 // z planes per work item: 16, halved (to no fewer than 4) while the items would not fill

@@ -49,22 +49,23 @@ static long long run_sweep(int nx, int ny, int nz, const int* per, const T* diag
     T* raw = reinterpret_cast<T*>(&S);
     const size_t nraw = sizeof(S) / sizeof(T);
     std::vector<sweep::Fetch<T>> F(sweep::kThreads);
+    std::vector<sweep::Item> I(sweep::kThreads);
     const long long nit = sweep::items(A.d, A.zc);
     // the CTAs of a launch with `grid` blocks, each taking items blockIdx, blockIdx + grid, ...
     for (int blk = 0; blk < grid; ++blk)
         for (long long it = blk; it < nit; it += grid) {
             for (size_t k = 0; k < nraw; ++k) raw[k] = std::numeric_limits<T>::quiet_NaN();
-            int X0, Y0, z0, z1;
-            sweep::item_origin(A.d, A.zc, it, X0, Y0, z0, z1);
-            for (int t = 0; t < sweep::kThreads; ++t) sweep::fetch(A, X0, Y0, z0 - 2, t, F[t]);
+            for (int t = 0; t < sweep::kThreads; ++t) sweep::item_setup(A, it, t, I[t]);
+            const int z0 = I[0].z0, z1 = I[0].z1;
+            for (int t = 0; t < sweep::kThreads; ++t) sweep::fetch(A, I[t], z0 - 2, F[t]);
             for (int p = z0 - 2; p <= z1 + 1; ++p) {
                 for (int t = 0; t < sweep::kThreads; ++t) sweep::stage(S, p, t, F[t]);
                 if (p < z1 + 1)
-                    for (int t = 0; t < sweep::kThreads; ++t) sweep::fetch(A, X0, Y0, p + 1, t, F[t]);
+                    for (int t = 0; t < sweep::kThreads; ++t) sweep::fetch(A, I[t], p + 1, F[t]);
                 if (p - 1 >= z0 - 1)
-                    for (int t = 0; t < nth; ++t) sweep::first_colour(A, S, X0, Y0, p - 1, z0, z1, t, nth);
+                    for (int t = 0; t < sweep::kThreads; ++t) sweep::first_colour(A, S, I[t], p - 1);
                 if (p - 2 >= z0)
-                    for (int t = 0; t < nth; ++t) sweep::second_colour(A, S, X0, Y0, p - 2, t, nth);
+                    for (int t = 0; t < sweep::kThreads; ++t) sweep::second_colour(A, S, I[t], p - 2);
             }
         }
     return g_bad_index;
