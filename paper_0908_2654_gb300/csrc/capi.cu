@@ -315,7 +315,7 @@ void smooth(rt_grid* g, Level<T>& L, int nu, int first, bool zero, const Level<T
         // the new iterate written once (no old iterate from zero; the coarse correction adds the
         // coarse level's x, 1/8 word per fine cell)
         const double words = (z0 ? 6.0 : 7.0) + (c ? 0.125 : 0.0);
-        run(g, cls, n * words * t, [&] { launch_rbgs_sweep<T>(L, first, z0, c, g->stream); });
+        run(g, cls, n * words * t, [&] { launch_rbgs_sweep<T>(L, first, z0, c, g->d_err, g->stream); });
         std::swap(L.x, L.xt);
     }
 }
@@ -371,8 +371,16 @@ int read_scalars(rt_grid* g, int nb, int nslots, double* out, int nmax = 0) {
     run(g, K_FINALIZE, 0.0, [&] { launch_finalize_ext(g->partials, nb, nslots, nmax, g->dots, g->stream); });
     nslots += nmax;
     RT_CUDA(cudaMemcpyAsync(g->h_pinned, g->dots, sizeof(double) * nslots, cudaMemcpyDeviceToHost, g->stream));
+    // the device error word rides along (the multigrid sweeps report there)
+    RT_CUDA(cudaMemcpyAsync(&g->h_pinned[63], g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
     RT_CUDA(cudaStreamSynchronize(g->stream));
     for (int k = 0; k < nslots; ++k) out[k] = g->h_pinned[k];
+    int herr = 0;
+    std::memcpy(&herr, &g->h_pinned[63], sizeof(int));
+    if (herr & 16) {
+        set_detail("a multigrid sweep gave up waiting for its shared-memory copies");
+        return RT_ECUDA;
+    }
     return check_launch("reduction");
 }
 

@@ -199,9 +199,12 @@ struct Level {
 template <class T>
 void launch_coarsen(const Level<T>& f, const Level<T>& c, cudaStream_t s);
 // one red-black Gauss-Seidel sweep (first colour `first`) from L.x into L.xt; from a zero iterate
-// (zero_guess) or from L.x plus the prolongation of coarse->x (coarse not null)
+// (zero_guess) or from L.x plus the prolongation of coarse->x (coarse not null).  Levels whose
+// rows allow it are staged by bulk tensor copies; a CTA that gives up waiting for its copies sets
+// bit 4 of *err (err may be null: then the copies are not used)
 template <class T>
-void launch_rbgs_sweep(const Level<T>& L, int first, bool zero_guess, const Level<T>* coarse, cudaStream_t s);
+void launch_rbgs_sweep(const Level<T>& L, int first, bool zero_guess, const Level<T>* coarse, int* err,
+                       cudaStream_t s);
 template <class T>
 void launch_resid_restrict(const Level<T>& f, const Level<T>& c, cudaStream_t s);
 template <class T>

@@ -16,8 +16,15 @@
 //        coefficients);
 //      - a single-CTA solver that runs the remaining coarse levels in shared memory and finishes
 //        with a dense Cholesky solve (or the exact 1-cell solve) on the coarsest one.
+#include <cuda.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "kernels.cuh"
 #include "smoother.cuh"
+#include "smoother_tma.cuh"
 
 namespace {
 
@@ -272,6 +279,124 @@ __global__ void __launch_bounds__(sweep::kThreads) k_rbgs_sweep(sweep::Args<T> A
             if (p - 2 >= I.z0) sweep::second_colour(A, S, I, p - 2);
             __syncthreads();
         }
+    }
+}
+
+// ---- TMA-fed sweep (smoother_tma.cuh): bulk tensor copies, mbarriers with bounded waits
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    unsigned long long state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                 : "=l"(state)
+                 : "r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    (void)state;
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    unsigned long long state;
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(bar)) : "memory");
+    (void)state;
+}
+// tries to see the phase with the given parity complete at most `limit` times (each try may
+// suspend the thread for a short, hardware-defined time); false when it never did
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit) {
+    const unsigned a = smem_u32(bar);
+    for (long long k = 0; k < limit; ++k) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+constexpr long long kWaitTries = 1LL << 21;
+
+template <class T>
+__global__ void __launch_bounds__(tsweep::kThreads) k_rbgs_sweep_tma(tsweep::Args<T> A, const __grid_constant__ CUtensorMap mb,
+                                                                  const __grid_constant__ CUtensorMap md,
+                                                                  const __grid_constant__ CUtensorMap mwx,
+                                                                  const __grid_constant__ CUtensorMap mwy,
+                                                                  const __grid_constant__ CUtensorMap mwz,
+                                                                  const __grid_constant__ CUtensorMap mx) {
+    using G = tsweep::Geom<T>;
+    extern __shared__ __align__(128) unsigned char smem_tsweep[];
+    tsweep::Tile<T>& S = *reinterpret_cast<tsweep::Tile<T>*>(smem_tsweep);
+    __shared__ int fail;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < G::NR; ++s) mbar_init(&S.bar[s], 1);
+        fail = 0;
+    }
+    __syncthreads();
+    const CUtensorMap* maps[tsweep::NARR] = {&mb, &md, &mwx, &mwy, &mwz, &mx};
+    constexpr unsigned tile_bytes = G::TILE * sizeof(T);
+    const int na = A.zero_guess ? tsweep::NARR - 1 : tsweep::NARR;   // no copy of a zero iterate
+    long long seq = 0;   // sequence number of the next plane this CTA consumes
+    const long long nit = sweep::items(A.d, A.zc);
+    for (long long it = blockIdx.x; it < nit; it += gridDim.x) {
+        tsweep::Item I;
+        tsweep::item_setup(A, it, tid, I);
+        const int p0 = I.z0 - 2, p1 = I.z1 + 1;
+        // thread 0: copies of plane p into its slot (a plane outside a non-periodic grid is not
+        // copied; its barrier phase is completed by a plain arrival)
+        auto issue = [&](int p, long long sq) {
+            const int s = tsweep::slot_of(sq, G::NR);
+            const int gz = sweep::gcoord(p, A.d.nz, A.d.per[2]);
+            if (gz < 0) {
+                mbar_arrive(&S.bar[s]);
+                return;
+            }
+            fence_proxy_async();   // the slot's earlier generic reads and writes come first
+            mbar_expect_tx(&S.bar[s], na * tile_bytes);
+#pragma unroll
+            for (int a = 0; a < tsweep::NARR; ++a)
+                if (a < na) tma_load_3d(S.t[s][a], maps[a], I.X0 - G::XOFF, I.Y0 - tsweep::HALO, gz, &S.bar[s]);
+        };
+        if (tid == 0)
+            for (int p = p0; p < p0 + G::D && p <= p1; ++p) issue(p, seq + (p - p0));
+        for (int p = p0; p <= p1; ++p) {
+            const long long sq = seq + (p - p0);
+            if (tid == 0 && p + G::D <= p1) issue(p + G::D, sq + G::D);
+            const int s = tsweep::slot_of(sq, G::NR);
+            if (!mbar_wait(&S.bar[s], (unsigned)((sq / G::NR) & 1), kWaitTries)) fail = 1;
+            tsweep::fix_plane(A, S, I, p, s, tid, blockDim.x);
+            __syncthreads();
+            if (fail) {
+                // give up: wait (bounded) for this CTA's copies still in flight, record, return
+                if (tid == 0) {
+                    const int last = p + G::D <= p1 ? p + G::D : p1;
+                    for (int q = p + 1; q <= last; ++q) {
+                        const long long sq2 = seq + (q - p0);
+                        mbar_wait(&S.bar[tsweep::slot_of(sq2, G::NR)], (unsigned)((sq2 / G::NR) & 1), kWaitTries);
+                    }
+                    atomicOr(A.err, 16);
+                }
+                return;
+            }
+            if (p - 1 >= p0 + 1) tsweep::first_colour(A, S, I, p - 1, sq - 1);
+            __syncthreads();
+            if (p - 2 >= I.z0) tsweep::second_colour(A, S, I, p - 2, sq - 2);
+            __syncthreads();
+        }
+        seq += p1 - p0 + 1;
     }
 }
 
@@ -682,8 +807,106 @@ int sm_count() {
 }
 }  // namespace
 
+// ---- tensor maps of the TMA-fed sweep
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, looked up once through the runtime (null if unavailable)
+EncodeTiled encoder() {
+    static EncodeTiled fn = nullptr;
+    static bool tried = false;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+// The tensor map of one level array for the sweep's box (cached per address and shape: the
+// level arrays live as long as their grid).  False if it cannot be encoded.
 template <class T>
-void launch_rbgs_sweep(const Level<T>& L, int first, bool zero_guess, const Level<T>* coarse, cudaStream_t s) {
+bool sweep_map(const T* base, const Dims& d, CUtensorMap* out) {
+    using G = tsweep::Geom<T>;
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, int, int>, CUtensorMap> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple((const void*)base, d.nx, d.ny, d.nz);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *out = it->second;
+        return true;
+    }
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    CUtensorMap m;
+    const cuuint64_t dim[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
+    const cuuint64_t stride[2] = {(cuuint64_t)d.nx * sizeof(T), (cuuint64_t)d.nx * d.ny * sizeof(T)};
+    const cuuint32_t box[3] = {(cuuint32_t)G::BX, (cuuint32_t)G::BY, 1};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    if (enc(&m, dt, 3, const_cast<T*>(base), dim, stride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    cache[key] = m;
+    *out = m;
+    return true;
+}
+
+// The TMA-fed sweep when the level allows it: no fused coarse correction, rows a multiple of
+// 16 bytes (the tensor's strides) and every array 16-byte aligned.  False when not launched.
+template <class T>
+bool launch_sweep_tma(const Level<T>& L, int first, bool zero_guess, int* err, cudaStream_t s) {
+    const Dims& d = L.d;
+    if ((d.nx * sizeof(T)) % 16 != 0) return false;
+    const T* arrs[6] = {L.b, L.diag, L.wx, L.wy, L.wz, L.x};
+    for (const T* a : arrs)
+        if (!a || (reinterpret_cast<uintptr_t>(a) % 16) != 0) return false;
+    CUtensorMap m[6];
+    for (int a = 0; a < 6; ++a)
+        if (!sweep_map<T>(arrs[a], d, &m[a])) return false;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaFuncSetAttribute(k_rbgs_sweep_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(tsweep::Tile<T>));
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbgs_sweep_tma<T>, tsweep::kThreads,
+                                                          sizeof(tsweep::Tile<T>)) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+    }
+    tsweep::Args<T> A;
+    A.d = geo_of(d);
+    A.b = L.b;
+    A.diag = L.diag;
+    A.wx = L.wx;
+    A.wy = L.wy;
+    A.wz = L.wz;
+    A.xin = L.x;
+    A.xout = L.xt;
+    A.first = first;
+    A.zero_guess = zero_guess ? 1 : 0;
+    const long long slots = (long long)sm_count() * per_sm;
+    A.zc = sweep::chunk_planes(A.d, slots);
+    A.err = err;
+    const long long nit = sweep::items(A.d, A.zc);
+    const int grid = (int)(nit < slots ? nit : slots);
+    k_rbgs_sweep_tma<T><<<grid, tsweep::kThreads, sizeof(tsweep::Tile<T>), s>>>(A, m[0], m[1], m[2], m[3], m[4], m[5]);
+    return true;
+}
+
+template <class T>
+void launch_rbgs_sweep(const Level<T>& L, int first, bool zero_guess, const Level<T>* coarse, int* err,
+                       cudaStream_t s) {
+    if (!coarse && err && launch_sweep_tma<T>(L, first, zero_guess, err, s)) return;
     // resident CTAs per SM of the sweep kernel (shared memory bound), found once per precision
     static int per_sm = 0;
     if (per_sm == 0) {
@@ -744,8 +967,8 @@ int launch_tail(const Level<T>& L, int ncycles, int nu, cudaStream_t s) {
 
 template void launch_coarsen<float>(const Level<float>&, const Level<float>&, cudaStream_t);
 template void launch_coarsen<double>(const Level<double>&, const Level<double>&, cudaStream_t);
-template void launch_rbgs_sweep<float>(const Level<float>&, int, bool, const Level<float>*, cudaStream_t);
-template void launch_rbgs_sweep<double>(const Level<double>&, int, bool, const Level<double>*, cudaStream_t);
+template void launch_rbgs_sweep<float>(const Level<float>&, int, bool, const Level<float>*, int*, cudaStream_t);
+template void launch_rbgs_sweep<double>(const Level<double>&, int, bool, const Level<double>*, int*, cudaStream_t);
 template void launch_resid_restrict<float>(const Level<float>&, const Level<float>&, cudaStream_t);
 template void launch_resid_restrict<double>(const Level<double>&, const Level<double>&, cudaStream_t);
 template int launch_tail<float>(const Level<float>&, int, int, cudaStream_t);

@@ -17,6 +17,7 @@ static long long g_bad_index = 0;
 #endif
 
 #include "../../paper_0908_2654_gb300/csrc/smoother.cuh"
+#include "../../paper_0908_2654_gb300/csrc/smoother_tma.cuh"
 
 template <class T>
 static long long run_sweep(int nx, int ny, int nz, const int* per, const T* diag, const T* wx, const T* wy, const T* wz,
@@ -92,5 +93,73 @@ int sweep_chunk_planes(int nx, int ny, int nz, long long slots) {
     d.nz = nz;
     d.per[0] = d.per[1] = d.per[2] = 0;
     return sweep::chunk_planes(d, slots);
+}
+}
+
+// the TMA-fed sweep, its copies emulated in the kernel's order: the copy of plane p + D lands at
+// the start of step p, in the slot plane p + D - NR held
+template <class T>
+static long long run_sweep_tma(int nx, int ny, int nz, const int* per, const T* diag, const T* wx, const T* wy,
+                               const T* wz, const T* b, const T* xin, T* xout, int first, int zero, int zc,
+                               int grid) {
+    using G = tsweep::Geom<T>;
+    g_bad_index = 0;
+    tsweep::Args<T> A;
+    A.d.nx = nx;
+    A.d.ny = ny;
+    A.d.nz = nz;
+    for (int k = 0; k < 3; ++k) A.d.per[k] = per[k];
+    A.b = b;
+    A.diag = diag;
+    A.wx = wx;
+    A.wy = wy;
+    A.wz = wz;
+    A.xin = xin;
+    A.xout = xout;
+    A.first = first;
+    A.zero_guess = zero;
+    A.zc = zc > 0 ? zc : sweep::chunk_planes(A.d, 152 * 3);
+    A.err = nullptr;
+    if (grid <= 0) grid = 1;
+    std::vector<tsweep::Tile<T>> tile(1);
+    tsweep::Tile<T>& S = tile[0];
+    T* raw = reinterpret_cast<T*>(&S.t[0][0][0]);
+    const size_t nraw = sizeof(S.t) / sizeof(T);
+    std::vector<tsweep::Item> I(tsweep::kThreads);
+    const long long nit = sweep::items(A.d, A.zc);
+    for (int blk = 0; blk < grid; ++blk) {
+        for (size_t k = 0; k < nraw; ++k) raw[k] = std::numeric_limits<T>::quiet_NaN();
+        long long seq = 0;
+        for (long long it = blk; it < nit; it += grid) {
+            for (int t = 0; t < tsweep::kThreads; ++t) tsweep::item_setup(A, it, t, I[t]);
+            const int p0 = I[0].z0 - 2, p1 = I[0].z1 + 1;
+            for (int p = p0; p < p0 + G::D && p <= p1; ++p)
+                tsweep::emulate_copy(A, S, I[0], p, tsweep::slot_of(seq + (p - p0), G::NR));
+            for (int p = p0; p <= p1; ++p) {
+                const long long sq = seq + (p - p0);
+                if (p + G::D <= p1) tsweep::emulate_copy(A, S, I[0], p + G::D, tsweep::slot_of(sq + G::D, G::NR));
+                const int s = tsweep::slot_of(sq, G::NR);
+                for (int t = 0; t < tsweep::kThreads; ++t) tsweep::fix_plane(A, S, I[t], p, s, t, tsweep::kThreads);
+                if (p - 1 >= p0 + 1)
+                    for (int t = 0; t < tsweep::kThreads; ++t) tsweep::first_colour(A, S, I[t], p - 1, sq - 1);
+                if (p - 2 >= I[0].z0)
+                    for (int t = 0; t < tsweep::kThreads; ++t) tsweep::second_colour(A, S, I[t], p - 2, sq - 2);
+            }
+            seq += p1 - p0 + 1;
+        }
+    }
+    return g_bad_index;
+}
+
+extern "C" {
+long long sweep_tma_host_f64(int nx, int ny, int nz, const int* per, const double* diag, const double* wx,
+                             const double* wy, const double* wz, const double* b, const double* xin, double* xout,
+                             int first, int zero, int zc, int grid) {
+    return run_sweep_tma<double>(nx, ny, nz, per, diag, wx, wy, wz, b, xin, xout, first, zero, zc, grid);
+}
+long long sweep_tma_host_f32(int nx, int ny, int nz, const int* per, const float* diag, const float* wx,
+                             const float* wy, const float* wz, const float* b, const float* xin, float* xout,
+                             int first, int zero, int zc, int grid) {
+    return run_sweep_tma<float>(nx, ny, nz, per, diag, wx, wy, wz, b, xin, xout, first, zero, zc, grid);
 }
 }

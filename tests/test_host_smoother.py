@@ -87,6 +87,19 @@ def _prolong_reference(xc, fshape, per):
     return out
 
 
+def _call_tma(lib, dtype, shape, per, diag, w, b, xin, first, zero, zc, grid=5):
+    nz, ny, nx = shape
+    fn = lib.sweep_tma_host_f64 if dtype == np.float64 else lib.sweep_tma_host_f32
+    fn.restype = ctypes.c_longlong
+    arr = lambda a: np.ascontiguousarray(a, dtype=dtype)
+    args = [arr(diag), *[arr(v) for v in w], arr(b), arr(xin)]
+    out = np.full(shape, np.nan, dtype=dtype)
+    perc = (ctypes.c_int * 3)(*per)
+    bad = fn(nx, ny, nz, perc, *[a.ctypes.data_as(ctypes.c_void_p) for a in args], out.ctypes.data_as(ctypes.c_void_p),
+             first, zero, zc, grid)
+    return out, bad
+
+
 def _call(lib, dtype, shape, per, diag, w, b, xin, first, zero, zc, xc=None, nth=256, grid=7):
     nz, ny, nx = shape
     fn = lib.sweep_host_f64 if dtype == np.float64 else lib.sweep_host_f32
@@ -122,6 +135,28 @@ def test_fused_sweep_equals_red_black_gauss_seidel(lib, shape, per, zc, dtype):
         np.testing.assert_allclose(got, ref, rtol=tol, atol=tol * np.abs(ref).max())
     ref0 = _rbgs_reference(diag, w, b, np.zeros(shape), 0)
     got, bad = _call(lib, dtype, shape, per, diag, w, b, np.full(shape, np.nan), 0, 1, zc)
+    assert bad == 0
+    np.testing.assert_allclose(got, ref0, rtol=tol, atol=tol * np.abs(ref0).max())
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("shape,per,zc", CASES)
+def test_tensor_copy_sweep_equals_red_black_gauss_seidel(lib, shape, per, zc, dtype):
+    """The sweep fed by bulk tensor copies (boxes with zeros outside the grid, wrapped edges of
+    periodic axes patched, planes copied ahead into a ring of slots), its copies emulated in the
+    kernel's order, against the plain sweep's definition."""
+    rng = np.random.default_rng(3 + sum(shape))
+    diag, *w = _operator(shape, per, rng, dtype)
+    b = rng.standard_normal(shape).astype(dtype)
+    x0 = rng.standard_normal(shape).astype(dtype)
+    tol = 1e-13 if dtype == np.float64 else 2e-6
+    for first in (0, 1):
+        ref = _rbgs_reference(diag, w, b, x0, first)
+        got, bad = _call_tma(lib, dtype, shape, per, diag, w, b, x0, first, 0, zc, grid=1 if first else 5)
+        assert bad == 0
+        np.testing.assert_allclose(got, ref, rtol=tol, atol=tol * np.abs(ref).max())
+    ref0 = _rbgs_reference(diag, w, b, np.zeros(shape), 1)
+    got, bad = _call_tma(lib, dtype, shape, per, diag, w, b, np.full(shape, np.nan), 1, 1, zc)
     assert bad == 0
     np.testing.assert_allclose(got, ref0, rtol=tol, atol=tol * np.abs(ref0).max())
 
