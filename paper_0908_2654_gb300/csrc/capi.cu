@@ -201,13 +201,13 @@ int check_launch(const char* what) {
 
 enum KClass {
     K_ZERO, K_SOURCES, K_FACES, K_SETUP, K_ASSEMBLE, K_FINALIZE, K_SPMV, K_RESNORM, K_CG_UPDATE, K_DOT2, K_P_UPDATE,
-    K_SCALARS, K_COPY, K_CAST, K_MG_DIAG, K_COARSEN, K_RBGS, K_RESTRICT, K_TAIL, K_ADD, K_ADVECT,
+    K_SCALARS, K_COPY, K_CAST, K_MG_DIAG, K_COARSEN, K_RBGS, K_RESTRICT, K_PROLONG, K_TAIL, K_ADD, K_ADVECT,
     K_ADVECT_CHECK, K_RBGS_FINE, K_NCLASS
 };
 const char* kClassName[K_NCLASS] = {"zero", "scatter_sources", "faces", "setup", "newton_assemble", "finalize",
                                     "cg_spmv_dot", "cg_residual", "cg_update_xr", "cg_dot2", "cg_p_update",
                                     "cg_scalars", "copy", "cast", "mg_diag", "mg_coarsen", "mg_rbgs",
-                                    "mg_resid_restrict", "mg_coarse_cta", "add", "advect",
+                                    "mg_resid_restrict", "mg_prolong_add", "mg_coarse_cta", "add", "advect",
                                     "advect_courant", "mg_rbgs_fine"};
 
 // Launch f() as kernel class cls moving `bytes` algorithmic bytes; brackets it with events
@@ -263,6 +263,9 @@ HierarchyStatus build_hierarchy(rt_grid* g, Hierarchy<T>& H, T* diag0, T* wx0, T
     L.x = nullptr;   // level 0 vectors are bound per solve
     L.xt = nullptr;
     L.b = nullptr;
+    L.counters = dalloc<unsigned>(1 + 512, ok);
+    H.owned.push_back(L.counters);
+    if (!ok) return HIER_NOMEM;
     H.lv.push_back(L);
     while (d.n() > TailMax<T>::value) {
         if (d.nx % 2 || d.ny % 2 || d.nz % 2) return HIER_ODD;
@@ -277,9 +280,10 @@ HierarchyStatus build_hierarchy(rt_grid* g, Hierarchy<T>& H, T* diag0, T* wx0, T
         c.wy = dalloc<T>(n, ok);
         c.wz = dalloc<T>(n, ok);
         c.x = dalloc<T>(n, ok);
-        c.xt = dalloc<T>(n, ok);
+        c.xt = nullptr;
         c.b = dalloc<T>(n, ok);
-        for (void* p : {(void*)c.diag, (void*)c.wx, (void*)c.wy, (void*)c.wz, (void*)c.x, (void*)c.xt, (void*)c.b})
+        c.counters = dalloc<unsigned>(1 + 512, ok);
+        for (void* p : {(void*)c.diag, (void*)c.wx, (void*)c.wy, (void*)c.wz, (void*)c.x, (void*)c.b, (void*)c.counters})
             H.owned.push_back(p);
         if (!ok) return HIER_NOMEM;
         H.lv.push_back(c);
@@ -320,8 +324,21 @@ void smooth(rt_grid* g, Level<T>& L, int nu, int first, bool zero, const Level<T
     }
 }
 
-// one V-cycle on the hierarchy: level-0 b, x and xt must be bound; the result is left in
-// level 0's x (which may be either of the two level-0 buffers)
+// nu red-black Gauss-Seidel sweeps of level L in place (first colour `first`); the first from a
+// zero iterate when `zero`
+template <class T>
+void smooth_inplace(rt_grid* g, Level<T>& L, int nu, int first, bool zero, int cls) {
+    const double n = (double)L.d.n(), t = sizeof(T);
+    for (int k = 0; k < nu; ++k) {
+        const bool z0 = zero && k == 0;
+        // algorithmic words per cell of a sweep: b, diag, wx, wy, wz and x read once, x written
+        // once (no read of x from a zero iterate)
+        const double words = z0 ? 6.0 : 7.0;
+        run(g, cls, n * words * t, [&] { launch_rbgs_inplace<T>(L, first, z0, g->d_err, g->stream); });
+    }
+}
+
+// one V-cycle on the hierarchy: level-0 b and x must be bound; the result is left in level 0's x
 template <class T>
 void vcycle(rt_grid* g, Hierarchy<T>& H) {
     const int nu1 = g->desc.mg_nu1, nu2 = g->desc.mg_nu2;
@@ -331,13 +348,16 @@ void vcycle(rt_grid* g, Hierarchy<T>& H) {
     for (int l = 0; l < last; ++l) {
         const double n = (double)H.lv[l].d.n();
         const int cls = l == 0 ? K_RBGS_FINE : K_RBGS;   // the fine level timed on its own
-        smooth<T>(g, H.lv[l], nu1, 0, true, nullptr, cls);
+        smooth_inplace<T>(g, H.lv[l], nu1, 0, true, cls);
         run(g, K_RESTRICT, n * 6.125 * t, [&] { launch_resid_restrict<T>(H.lv[l], H.lv[l + 1], s); });
     }
     run(g, K_TAIL, (double)H.lv[last].d.n() * 6 * t, [&] { launch_tail<T>(H.lv[last], 1, std::max(nu1, 1), s); });
     for (int l = last - 1; l >= 0; --l) {
+        const double n = (double)H.lv[l].d.n();
         const int cls = l == 0 ? K_RBGS_FINE : K_RBGS;
-        smooth<T>(g, H.lv[l], nu2, 1, false, &H.lv[l + 1], cls);
+        // fine x read and written, the coarse correction read (1/8 word per fine cell)
+        run(g, K_PROLONG, n * 2.125 * t, [&] { launch_prolong_add<T>(H.lv[l + 1], H.lv[l], s); });
+        smooth_inplace<T>(g, H.lv[l], nu2, 1, false, cls);
     }
 }
 
@@ -377,8 +397,8 @@ int read_scalars(rt_grid* g, int nb, int nslots, double* out, int nmax = 0) {
     for (int k = 0; k < nslots; ++k) out[k] = g->h_pinned[k];
     int herr = 0;
     std::memcpy(&herr, &g->h_pinned[63], sizeof(int));
-    if (herr & 16) {
-        set_detail("a multigrid sweep gave up waiting for its shared-memory copies");
+    if (herr & 48) {
+        set_detail("a multigrid sweep gave up waiting (%s)", herr & 16 ? "shared-memory copies" : "a colour pass");
         return RT_ECUDA;
     }
     return check_launch("reduction");

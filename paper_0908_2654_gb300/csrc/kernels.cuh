@@ -195,6 +195,7 @@ struct Level {
     T* x;      // current iterate
     T* xt;     // second iterate buffer: a sweep reads x and writes xt, then the two swap
     T* b;
+    unsigned* counters;   // work counters of the in-place sweep (1 + up to rbq::kMaxPasses / 2)
 };
 template <class T>
 void launch_coarsen(const Level<T>& f, const Level<T>& c, cudaStream_t s);
@@ -205,6 +206,13 @@ void launch_coarsen(const Level<T>& f, const Level<T>& c, cudaStream_t s);
 template <class T>
 void launch_rbgs_sweep(const Level<T>& L, int first, bool zero_guess, const Level<T>* coarse, int* err,
                        cudaStream_t s);
+// one red-black Gauss-Seidel sweep of L.x in place, its two colour passes ordered so that the
+// second finds its data in L2; a CTA that gives up waiting sets bit 5 of *err
+template <class T>
+void launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, int* err, cudaStream_t s);
+// f.x += trilinear prolongation of c.x
+template <class T>
+void launch_prolong_add(const Level<T>& c, const Level<T>& f, cudaStream_t s);
 template <class T>
 void launch_resid_restrict(const Level<T>& f, const Level<T>& c, cudaStream_t s);
 template <class T>

@@ -25,6 +25,7 @@
 #include "kernels.cuh"
 #include "smoother.cuh"
 #include "smoother_tma.cuh"
+#include "rbqueue.cuh"
 
 namespace {
 
@@ -397,6 +398,89 @@ __global__ void __launch_bounds__(tsweep::kThreads) k_rbgs_sweep_tma(tsweep::Arg
             __syncthreads();
         }
         seq += p1 - p0 + 1;
+    }
+}
+
+// ---- in-place red-black sweep as two colour passes ordered for L2 reuse (rbqueue.cuh)
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+constexpr long long kQueueWaitTries = 1LL << 24;
+
+template <class T>
+__global__ void __launch_bounds__(rbq::kThreads) k_rbgs_queue(rbq::Args<T> A) {
+    __shared__ unsigned item;
+    __shared__ int give_up;
+    const rbq::Plan& P = A.P;
+    const unsigned nitems = 2u * (unsigned)P.nslab * (unsigned)P.chunks;
+    const int tid = threadIdx.x;
+    // x changes during the kernel: read it from L2, never from a stale L1 line
+    auto ld = [&](long long j) { return __ldcg(A.x + j); };
+    for (;;) {
+        if (tid == 0) item = atomicAdd(A.next, 1u);
+        __syncthreads();
+        const unsigned s = item;
+        __syncthreads();
+        if (s >= nitems) break;
+        int k, pass;
+        rbq::pass_of(P, (int)(s / (unsigned)P.chunks), k, pass);
+        const int c = (int)(s % (unsigned)P.chunks);
+        if (pass == 1) {
+            // the first passes over slabs k - 1, k and k + 1 must be complete
+            if (tid == 0) {
+                give_up = 0;
+                for (int dk = -1; dk <= 1 && !give_up; ++dk) {
+                    int kk = k + dk;
+                    if (kk < 0 || kk >= P.nslab) {
+                        if (!P.per[2]) continue;
+                        kk = (kk + P.nslab) % P.nslab;
+                    }
+                    long long tries = 0;
+                    while (ld_acquire(A.done + kk) < (unsigned)P.chunks) {
+                        if (++tries > kQueueWaitTries) {
+                            give_up = 1;
+                            break;
+                        }
+                        __nanosleep(100);
+                    }
+                }
+                if (give_up) atomicOr(A.err, 32);
+            }
+            __syncthreads();
+            if (give_up) continue;
+        }
+        rbq::chunk_pass(A, k, c, pass, tid, blockDim.x, ld);
+        if (pass == 0) {
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                atomicAdd(A.done + k, 1u);
+            }
+        }
+    }
+}
+
+// x += P xc: trilinear cell-centred prolongation of the coarse correction
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_prolong_add(Level<T> c, Level<T> f) {
+    const Dims fd = f.d;
+    const int nxy = fd.nx * fd.ny;
+    const long long n = fd.n();
+    sweep::Args<T> A;
+    A.xc = c.x;
+    A.cd.nx = c.d.nx;
+    A.cd.ny = c.d.ny;
+    A.cd.nz = c.d.nz;
+    for (int k = 0; k < 3; ++k) A.cd.per[k] = c.d.per[k];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int z = (int)(i / nxy);
+        const int r = (int)(i - (long long)z * nxy);
+        const int y = r / fd.nx, x = r - y * fd.nx;
+        f.x[i] += sweep::prolong_at(A, x, y, z);
     }
 }
 
@@ -904,6 +988,38 @@ bool launch_sweep_tma(const Level<T>& L, int first, bool zero_guess, int* err, c
 }
 
 template <class T>
+void launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, int* err, cudaStream_t s) {
+    static int per_sm = 0;
+    if (per_sm == 0 &&
+        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbgs_queue<T>, rbq::kThreads, 0) != cudaSuccess ||
+         per_sm < 1))
+        per_sm = 1;
+    rbq::Args<T> A;
+    A.P = rbq::make_plan(L.d.nx, L.d.ny, L.d.nz, L.d.per);
+    A.diag = L.diag;
+    A.wx = L.wx;
+    A.wy = L.wy;
+    A.wz = L.wz;
+    A.b = L.b;
+    A.x = L.x;
+    A.first = first;
+    A.zero_guess = zero_guess ? 1 : 0;
+    A.next = L.counters;
+    A.done = L.counters + 1;
+    A.err = err;
+    cudaMemsetAsync(L.counters, 0, sizeof(unsigned) * (1 + A.P.nslab), s);
+    const long long nitems = 2LL * A.P.nslab * A.P.chunks;
+    const long long slots = (long long)sm_count() * per_sm;
+    const int grid = (int)(nitems < slots ? nitems : slots);
+    k_rbgs_queue<T><<<grid, rbq::kThreads, 0, s>>>(A);
+}
+
+template <class T>
+void launch_prolong_add(const Level<T>& c, const Level<T>& f, cudaStream_t s) {
+    k_prolong_add<T><<<grid_for(f.d.n()), kBlock, 0, s>>>(c, f);
+}
+
+template <class T>
 void launch_rbgs_sweep(const Level<T>& L, int first, bool zero_guess, const Level<T>* coarse, int* err,
                        cudaStream_t s) {
     if (!coarse && err && launch_sweep_tma<T>(L, first, zero_guess, err, s)) return;
@@ -968,6 +1084,10 @@ int launch_tail(const Level<T>& L, int ncycles, int nu, cudaStream_t s) {
 template void launch_coarsen<float>(const Level<float>&, const Level<float>&, cudaStream_t);
 template void launch_coarsen<double>(const Level<double>&, const Level<double>&, cudaStream_t);
 template void launch_rbgs_sweep<float>(const Level<float>&, int, bool, const Level<float>*, int*, cudaStream_t);
+template void launch_rbgs_inplace<float>(const Level<float>&, int, bool, int*, cudaStream_t);
+template void launch_rbgs_inplace<double>(const Level<double>&, int, bool, int*, cudaStream_t);
+template void launch_prolong_add<float>(const Level<float>&, const Level<float>&, cudaStream_t);
+template void launch_prolong_add<double>(const Level<double>&, const Level<double>&, cudaStream_t);
 template void launch_rbgs_sweep<double>(const Level<double>&, int, bool, const Level<double>*, int*, cudaStream_t);
 template void launch_resid_restrict<float>(const Level<float>&, const Level<float>&, cudaStream_t);
 template void launch_resid_restrict<double>(const Level<double>&, const Level<double>&, cudaStream_t);

@@ -18,6 +18,7 @@ static long long g_bad_index = 0;
 
 #include "../../paper_0908_2654_gb300/csrc/smoother.cuh"
 #include "../../paper_0908_2654_gb300/csrc/smoother_tma.cuh"
+#include "../../paper_0908_2654_gb300/csrc/rbqueue.cuh"
 
 template <class T>
 static long long run_sweep(int nx, int ny, int nz, const int* per, const T* diag, const T* wx, const T* wy, const T* wz,
@@ -161,5 +162,68 @@ long long sweep_tma_host_f32(int nx, int ny, int nz, const int* per, const float
                              const float* wy, const float* wz, const float* b, const float* xin, float* xout,
                              int first, int zero, int zc, int grid) {
     return run_sweep_tma<float>(nx, ny, nz, per, diag, wx, wy, wz, b, xin, xout, first, zero, zc, grid);
+}
+}
+
+// the in-place sweep of rbqueue.cuh: its work items in queue order, each chunk's threads one
+// after another (the order a single CTA would take them; the dependencies hold by construction)
+template <class T>
+static long long run_sweep_queue(int nx, int ny, int nz, const int* per, const T* diag, const T* wx, const T* wy,
+                                 const T* wz, const T* b, T* x, int first, int zero) {
+    g_bad_index = 0;
+    rbq::Args<T> A;
+    A.P = rbq::make_plan(nx, ny, nz, per);
+    A.diag = diag;
+    A.wx = wx;
+    A.wy = wy;
+    A.wz = wz;
+    A.b = b;
+    A.x = x;
+    A.first = first;
+    A.zero_guess = zero;
+    const long long n = (long long)nx * ny * nz;
+    auto ld = [&](long long j) {
+        if (!(j >= 0 && j < n)) ++g_bad_index;
+        return x[j];
+    };
+    const unsigned nitems = 2u * (unsigned)A.P.nslab * (unsigned)A.P.chunks;
+    std::vector<int> done(A.P.nslab, 0);
+    for (unsigned s = 0; s < nitems; ++s) {
+        int k, pass;
+        rbq::pass_of(A.P, (int)(s / (unsigned)A.P.chunks), k, pass);
+        const int c = (int)(s % (unsigned)A.P.chunks);
+        if (pass == 1)
+            for (int dk = -1; dk <= 1; ++dk) {
+                int kk = k + dk;
+                if (kk < 0 || kk >= A.P.nslab) {
+                    if (!per[2]) continue;
+                    kk = (kk + A.P.nslab) % A.P.nslab;
+                }
+                if (done[kk] < A.P.chunks) ++g_bad_index;   // a second pass before its first passes
+            }
+        for (int t = 0; t < rbq::kThreads; ++t) rbq::chunk_pass(A, k, c, pass, t, rbq::kThreads, ld);
+        if (pass == 0) ++done[k];
+    }
+    return g_bad_index;
+}
+
+extern "C" {
+long long sweep_queue_host_f64(int nx, int ny, int nz, const int* per, const double* diag, const double* wx,
+                               const double* wy, const double* wz, const double* b, double* x, int first, int zero) {
+    return run_sweep_queue<double>(nx, ny, nz, per, diag, wx, wy, wz, b, x, first, zero);
+}
+long long sweep_queue_host_f32(int nx, int ny, int nz, const int* per, const float* diag, const float* wx,
+                               const float* wy, const float* wz, const float* b, float* x, int first, int zero) {
+    return run_sweep_queue<float>(nx, ny, nz, per, diag, wx, wy, wz, b, x, first, zero);
+}
+int queue_plan(int nx, int ny, int nz, int pz, int* out) {
+    const int per[3] = {0, 0, pz};
+    const rbq::Plan P = rbq::make_plan(nx, ny, nz, per);
+    out[0] = P.slab;
+    out[1] = P.nslab;
+    out[2] = P.rows;
+    out[3] = P.row_blocks;
+    out[4] = P.chunks;
+    return 0;
 }
 }

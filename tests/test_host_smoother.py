@@ -100,6 +100,19 @@ def _call_tma(lib, dtype, shape, per, diag, w, b, xin, first, zero, zc, grid=5):
     return out, bad
 
 
+def _call_queue(lib, dtype, shape, per, diag, w, b, xin, first, zero):
+    nz, ny, nx = shape
+    fn = lib.sweep_queue_host_f64 if dtype == np.float64 else lib.sweep_queue_host_f32
+    fn.restype = ctypes.c_longlong
+    arr = lambda a: np.ascontiguousarray(a, dtype=dtype)
+    args = [arr(diag), *[arr(v) for v in w], arr(b)]
+    x = np.array(xin, dtype=dtype, copy=True)
+    perc = (ctypes.c_int * 3)(*per)
+    bad = fn(nx, ny, nz, perc, *[a.ctypes.data_as(ctypes.c_void_p) for a in args], x.ctypes.data_as(ctypes.c_void_p),
+             first, zero)
+    return x, bad
+
+
 def _call(lib, dtype, shape, per, diag, w, b, xin, first, zero, zc, xc=None, nth=256, grid=7):
     nz, ny, nx = shape
     fn = lib.sweep_host_f64 if dtype == np.float64 else lib.sweep_host_f32
@@ -159,6 +172,43 @@ def test_tensor_copy_sweep_equals_red_black_gauss_seidel(lib, shape, per, zc, dt
     got, bad = _call_tma(lib, dtype, shape, per, diag, w, b, np.full(shape, np.nan), 1, 1, zc)
     assert bad == 0
     np.testing.assert_allclose(got, ref0, rtol=tol, atol=tol * np.abs(ref0).max())
+
+
+QCASES = CASES + [((40, 16, 16), (True, False, True), 0), ((37, 8, 10), (False, True, False), 0),
+                  ((24, 6, 8), (True, True, False), 0)]
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("shape,per,zc", QCASES)
+def test_queued_in_place_sweep_equals_red_black_gauss_seidel(lib, shape, per, zc, dtype):
+    """The in-place sweep whose two colour passes are cut into slab chunks and queued (R0, R1,
+    B0, R2, B1, ...; periodic z: B0 last), run item by item in queue order, against the plain
+    sweep's definition; every second-pass chunk finds the first passes over its own and the
+    neighbouring slabs complete, and every index lies in the grid (odd nz too)."""
+    rng = np.random.default_rng(11 + sum(shape))
+    diag, *w = _operator(shape, per, rng, dtype)
+    b = rng.standard_normal(shape).astype(dtype)
+    x0 = rng.standard_normal(shape).astype(dtype)
+    tol = 1e-13 if dtype == np.float64 else 2e-6
+    for first in (0, 1):
+        ref = _rbgs_reference(diag, w, b, x0, first)
+        got, bad = _call_queue(lib, dtype, shape, per, diag, w, b, x0, first, 0)
+        assert bad == 0
+        np.testing.assert_allclose(got, ref, rtol=tol, atol=tol * np.abs(ref).max())
+    ref0 = _rbgs_reference(diag, w, b, np.zeros(shape), 0)
+    got, bad = _call_queue(lib, dtype, shape, per, diag, w, b, np.full(shape, np.nan), 0, 1)
+    assert bad == 0
+    np.testing.assert_allclose(got, ref0, rtol=tol, atol=tol * np.abs(ref0).max())
+
+
+def test_queue_plan(lib):
+    """Slabs of 8 planes (all of a thinner grid), chunks of 2048 cells' rows: 256^3 gives 32 slabs
+    of 8 planes x 32 row blocks of 8 rows."""
+    out = (ctypes.c_int * 5)()
+    lib.queue_plan(256, 256, 256, 1, out)
+    assert list(out) == [8, 32, 8, 32, 256]
+    lib.queue_plan(16, 16, 4, 0, out)
+    assert list(out) == [4, 1, 16, 1, 4]
 
 
 @pytest.mark.parametrize("shape,per,zc", [CASES[0], CASES[1], CASES[3], CASES[4]])
