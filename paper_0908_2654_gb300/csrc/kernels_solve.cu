@@ -413,18 +413,20 @@ constexpr long long kQueueWaitTries = 1LL << 24;
 
 template <class T>
 __global__ void __launch_bounds__(rbq::kThreads) k_rbgs_queue(rbq::Args<T> A) {
-    __shared__ unsigned item;
+    __shared__ unsigned next_item;
     __shared__ int give_up;
     const rbq::Plan& P = A.P;
     const unsigned nitems = 2u * (unsigned)P.nslab * (unsigned)P.chunks;
+    const unsigned complete = (unsigned)P.chunks * (rbq::kThreads / 32);   // warps that finish a pass
     const int tid = threadIdx.x;
     // x changes during the kernel: read it from L2, never from a stale L1 line
     auto ld = [&](long long j) { return __ldcg(A.x + j); };
+    if (tid == 0) next_item = atomicAdd(A.next, 1u);
+    __syncthreads();
+    unsigned s = next_item;
     for (;;) {
-        if (tid == 0) item = atomicAdd(A.next, 1u);
-        __syncthreads();
-        const unsigned s = item;
-        __syncthreads();
+        __syncthreads();                                   // every thread has read next_item
+        if (tid == 0) next_item = atomicAdd(A.next, 1u);   // the following item, fetched meanwhile
         if (s >= nitems) break;
         int k, pass;
         rbq::pass_of(P, (int)(s / (unsigned)P.chunks), k, pass);
@@ -440,7 +442,7 @@ __global__ void __launch_bounds__(rbq::kThreads) k_rbgs_queue(rbq::Args<T> A) {
                         kk = (kk + P.nslab) % P.nslab;
                     }
                     long long tries = 0;
-                    while (ld_acquire(A.done + kk) < (unsigned)P.chunks) {
+                    while (ld_acquire(A.done + kk) < complete) {
                         if (++tries > kQueueWaitTries) {
                             give_up = 1;
                             break;
@@ -451,16 +453,18 @@ __global__ void __launch_bounds__(rbq::kThreads) k_rbgs_queue(rbq::Args<T> A) {
                 if (give_up) atomicOr(A.err, 32);
             }
             __syncthreads();
-            if (give_up) continue;
-        }
-        rbq::chunk_pass(A, k, c, pass, tid, blockDim.x, ld);
-        if (pass == 0) {
-            __syncthreads();
-            if (tid == 0) {
+            if (!give_up) rbq::chunk_pass(A, k, c, pass, tid, blockDim.x, ld);
+        } else {
+            rbq::chunk_pass(A, k, c, pass, tid, blockDim.x, ld);
+            // each warp signals its part of the chunk once its stores are visible
+            __syncwarp();
+            if ((tid & 31) == 0) {
                 __threadfence();
                 atomicAdd(A.done + k, 1u);
             }
         }
+        __syncthreads();                                   // next_item has been written
+        s = next_item;
     }
 }
 

@@ -188,8 +188,9 @@ __device__ __forceinline__ LocalOut local_block(const PhysParams& P, const HCell
     return o;
 }
 
+// two CTAs per SM (128 registers a thread): twice the warps the FP64 pipe can switch between
 template <bool ISO, bool GIVEN>
-__global__ void __launch_bounds__(kBlock) k_assemble(PhysParams P, AssembleArgs A) {
+__global__ void __launch_bounds__(kBlock, 2) k_assemble(PhysParams P, AssembleArgs A) {
     const long long n = (long long)P.nx * P.ny * P.nz;
     const double inv_a3 = 1.0 / P.a3;
     const double kEa = P.kE * inv_a3;     // proper opacity per unit n_HI

@@ -8,7 +8,7 @@
 // update x in place.
 //
 // The grid is cut into slabs of `slab` z planes and each colour pass over a slab into chunks (a
-// plane and a block of rows, about 2048 cells).  Work items are taken from a counter in a fixed
+// plane and a block of rows, about 8192 cells).  Work items are taken from a counter in a fixed
 // queue order in which the second pass over slab k comes right after the first pass over slab
 // k + 1:  R0, R1, B0, R2, B1, ..., R(K-1), B(K-2), B(K-1)  (periodic z: B0 moves to the end, as
 // it needs R(K-1)).  So the slab's arrays, read from HBM by its first pass, are still in L2 when
@@ -107,7 +107,8 @@ struct Args {
     int first;
     int zero_guess;
     unsigned* next;   // work-item counter (zero at launch)
-    unsigned* done;   // finished first-pass chunks per slab (zero at launch)
+    unsigned* done;   // finished first-pass chunk-warps per slab (zero at launch): a pass over a
+                      // slab is complete at chunks x warps per CTA
     int* err;         // bit 5 (value 32) when a CTA gave up waiting
 };
 
@@ -146,7 +147,9 @@ RT_HD T cell_update(const Args<T>& A, int x, int y, int z, bool zero, LD ld) {
 }
 
 // one thread's part of chunk (slab k, chunk c) of a colour pass: pairs p = tid, tid + nth, ...
-// of the chunk's rows, the pair's cell of this pass's colour
+// of the chunk's rows, the pair's cell of this pass's colour.  The pairs are taken four at a
+// time, their new values all computed before any is stored (a store could otherwise keep the
+// next pair's loads from being issued early)
 template <class T, class LD>
 RT_HD void chunk_pass(const Args<T>& A, int k, int c, int pass, int tid, int nth, LD ld) {
     const Plan& P = A.P;
@@ -157,25 +160,38 @@ RT_HD void chunk_pass(const Args<T>& A, int k, int c, int pass, int tid, int nth
     const bool zero = pass == 0 && A.zero_guess;
     const int hp = (P.nx + 1) / 2;            // pairs per row
     const int npairs = hp * (y1 - y0);
-    for (int p = tid; p < npairs; p += nth) {
-        const int ry = p / hp, px = p - ry * hp;
-        const int y = y0 + ry;
-        const int x = 2 * px + ((2 * px + y + z + colour) & 1);   // the pair's cell of this colour
-        if (x >= P.nx) continue;
-        const T v = cell_update(A, x, y, z, zero, ld);
-        A.x[(long long)z * P.nx * P.ny + (long long)y * P.nx + x] = v;
+    constexpr int U = 4;
+    for (int base = 0; base < npairs; base += U * nth) {
+        T v[U];
+        int xs[U], ys[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int p = base + u * nth + tid;
+            xs[u] = -1;
+            if (p >= npairs) continue;
+            const int ry = p / hp, px = p - ry * hp;
+            const int y = y0 + ry;
+            const int x = 2 * px + ((2 * px + y + z + colour) & 1);   // the pair's cell of this colour
+            if (x >= P.nx) continue;
+            xs[u] = x;
+            ys[u] = y;
+            v[u] = cell_update(A, x, y, z, zero, ld);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (xs[u] >= 0) A.x[(long long)z * P.nx * P.ny + (long long)ys[u] * P.nx + xs[u]] = v[u];
     }
 }
 
-// the plan of a level: slabs of 8 planes (fewer on small levels, so that a pass spans several
-// chunks), chunks of about 2048 cells
+// the plan of a level: slabs of 8 planes (all planes of a thinner grid), chunks of about 8192
+// cells
 inline Plan make_plan(int nx, int ny, int nz, const int* per) {
     Plan P;
     P.nx = nx;
     P.ny = ny;
     P.nz = nz;
     for (int k = 0; k < 3; ++k) P.per[k] = per[k];
-    int rows = 2048 / (nx > 0 ? nx : 1);
+    int rows = 8192 / (nx > 0 ? nx : 1);
     if (rows < 1) rows = 1;
     if (rows > ny) rows = ny;
     P.rows = rows;

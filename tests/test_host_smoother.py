@@ -202,11 +202,11 @@ def test_queued_in_place_sweep_equals_red_black_gauss_seidel(lib, shape, per, zc
 
 
 def test_queue_plan(lib):
-    """Slabs of 8 planes (all of a thinner grid), chunks of 2048 cells' rows: 256^3 gives 32 slabs
-    of 8 planes x 32 row blocks of 8 rows."""
+    """Slabs of 8 planes (all of a thinner grid), chunks of 8192 cells' rows: 256^3 gives 32 slabs
+    of 8 planes x 8 row blocks of 32 rows."""
     out = (ctypes.c_int * 5)()
     lib.queue_plan(256, 256, 256, 1, out)
-    assert list(out) == [8, 32, 8, 32, 256]
+    assert list(out) == [8, 32, 32, 8, 64]
     lib.queue_plan(16, 16, 4, 0, out)
     assert list(out) == [4, 1, 16, 1, 4]
 
