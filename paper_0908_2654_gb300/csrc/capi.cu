@@ -334,7 +334,9 @@ void smooth_inplace(rt_grid* g, Level<T>& L, int nu, int first, bool zero, int c
         // algorithmic words per cell of a sweep: b, diag, wx, wy, wz and x read once, x written
         // once (no read of x from a zero iterate)
         const double words = z0 ? 6.0 : 7.0;
-        run(g, cls, n * words * t, [&] { launch_rbgs_inplace<T>(L, first, z0, g->d_err, g->stream); });
+        int nl = 1;
+        run(g, cls, n * words * t, [&] { nl = launch_rbgs_inplace<T>(L, first, z0, g->d_err, g->stream); });
+        g->launches += nl - 1;
     }
 }
 

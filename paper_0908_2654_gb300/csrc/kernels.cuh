@@ -206,10 +206,10 @@ void launch_coarsen(const Level<T>& f, const Level<T>& c, cudaStream_t s);
 template <class T>
 void launch_rbgs_sweep(const Level<T>& L, int first, bool zero_guess, const Level<T>* coarse, int* err,
                        cudaStream_t s);
-// one red-black Gauss-Seidel sweep of L.x in place, its two colour passes ordered so that the
-// second finds its data in L2; a CTA that gives up waiting sets bit 5 of *err
+// one red-black Gauss-Seidel sweep of L.x in place: colour passes launched slab by slab so that
+// the second pass over a slab finds its data in L2 (rbpass.cuh); returns the launches made
 template <class T>
-void launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, int* err, cudaStream_t s);
+int launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, int* err, cudaStream_t s);
 // f.x += trilinear prolongation of c.x
 template <class T>
 void launch_prolong_add(const Level<T>& c, const Level<T>& f, cudaStream_t s);

@@ -26,6 +26,7 @@
 #include "smoother.cuh"
 #include "smoother_tma.cuh"
 #include "rbqueue.cuh"
+#include "rbpass.cuh"
 
 namespace {
 
@@ -466,6 +467,14 @@ __global__ void __launch_bounds__(rbq::kThreads) k_rbgs_queue(rbq::Args<T> A) {
         __syncthreads();                                   // next_item has been written
         s = next_item;
     }
+}
+
+// one colour pass of a red-black sweep over planes [z0, z0 + gridDim.z) in place (rbpass.cuh)
+template <class T>
+__global__ void __launch_bounds__(rbp::kPairs) k_rbgs_pass(rbp::Pass<T> A) {
+    int x, y, z;
+    if (!rbp::pair_cell(A, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, x, y, z)) return;
+    A.x[(long long)z * A.nx * A.ny + (long long)y * A.nx + x] = rbp::cell_value(A, x, y, z);
 }
 
 // x += P xc: trilinear cell-centred prolongation of the coarse correction
@@ -992,30 +1001,34 @@ bool launch_sweep_tma(const Level<T>& L, int first, bool zero_guess, int* err, c
 }
 
 template <class T>
-void launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, int* err, cudaStream_t s) {
-    static int per_sm = 0;
-    if (per_sm == 0 &&
-        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbgs_queue<T>, rbq::kThreads, 0) != cudaSuccess ||
-         per_sm < 1))
-        per_sm = 1;
-    rbq::Args<T> A;
-    A.P = rbq::make_plan(L.d.nx, L.d.ny, L.d.nz, L.d.per);
-    A.diag = L.diag;
-    A.wx = L.wx;
-    A.wy = L.wy;
-    A.wz = L.wz;
-    A.b = L.b;
-    A.x = L.x;
-    A.first = first;
-    A.zero_guess = zero_guess ? 1 : 0;
-    A.next = L.counters;
-    A.done = L.counters + 1;
-    A.err = err;
-    cudaMemsetAsync(L.counters, 0, sizeof(unsigned) * (1 + A.P.nslab), s);
-    const long long nitems = 2LL * A.P.nslab * A.P.chunks;
-    const long long slots = (long long)sm_count() * per_sm;
-    const int grid = (int)(nitems < slots ? nitems : slots);
-    k_rbgs_queue<T><<<grid, rbq::kThreads, 0, s>>>(A);
+int launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, int* err, cudaStream_t s) {
+    (void)err;
+    const Dims& d = L.d;
+    const int S = rbp::slab_planes(d.nx, d.ny, d.nz, (int)sizeof(T));
+    const int K = (d.nz + S - 1) / S;
+    for (int j = 0; j < 2 * K; ++j) {
+        int slab, pass;
+        rbp::launch_of(K, d.per[2], j, slab, pass);
+        rbp::Pass<T> A;
+        A.nx = d.nx;
+        A.ny = d.ny;
+        A.nz = d.nz;
+        for (int k = 0; k < 3; ++k) A.per[k] = d.per[k];
+        A.diag = L.diag;
+        A.wx = L.wx;
+        A.wy = L.wy;
+        A.wz = L.wz;
+        A.b = L.b;
+        A.x = L.x;
+        A.colour = pass == 0 ? first : 1 - first;
+        A.zero = pass == 0 && zero_guess;
+        A.z0 = slab * S;
+        const int planes = A.z0 + S <= d.nz ? S : d.nz - A.z0;
+        int gx, gy, gz;
+        rbp::pass_grid(d.nx, d.ny, planes, gx, gy, gz, A.rows);
+        k_rbgs_pass<T><<<dim3(gx, gy, gz), rbp::kPairs, 0, s>>>(A);
+    }
+    return 2 * K;
 }
 
 template <class T>
@@ -1088,8 +1101,8 @@ int launch_tail(const Level<T>& L, int ncycles, int nu, cudaStream_t s) {
 template void launch_coarsen<float>(const Level<float>&, const Level<float>&, cudaStream_t);
 template void launch_coarsen<double>(const Level<double>&, const Level<double>&, cudaStream_t);
 template void launch_rbgs_sweep<float>(const Level<float>&, int, bool, const Level<float>*, int*, cudaStream_t);
-template void launch_rbgs_inplace<float>(const Level<float>&, int, bool, int*, cudaStream_t);
-template void launch_rbgs_inplace<double>(const Level<double>&, int, bool, int*, cudaStream_t);
+template int launch_rbgs_inplace<float>(const Level<float>&, int, bool, int*, cudaStream_t);
+template int launch_rbgs_inplace<double>(const Level<double>&, int, bool, int*, cudaStream_t);
 template void launch_prolong_add<float>(const Level<float>&, const Level<float>&, cudaStream_t);
 template void launch_prolong_add<double>(const Level<double>&, const Level<double>&, cudaStream_t);
 template void launch_rbgs_sweep<double>(const Level<double>&, int, bool, const Level<double>*, int*, cudaStream_t);

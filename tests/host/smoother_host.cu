@@ -19,6 +19,7 @@ static long long g_bad_index = 0;
 #include "../../paper_0908_2654_gb300/csrc/smoother.cuh"
 #include "../../paper_0908_2654_gb300/csrc/smoother_tma.cuh"
 #include "../../paper_0908_2654_gb300/csrc/rbqueue.cuh"
+#include "../../paper_0908_2654_gb300/csrc/rbpass.cuh"
 
 template <class T>
 static long long run_sweep(int nx, int ny, int nz, const int* per, const T* diag, const T* wx, const T* wy, const T* wz,
@@ -225,5 +226,70 @@ int queue_plan(int nx, int ny, int nz, int pz, int* out) {
     out[3] = P.row_blocks;
     out[4] = P.chunks;
     return 0;
+}
+}
+
+// the slab-ordered colour passes of rbpass.cuh, every block and thread of each launch in turn
+template <class T>
+static long long run_sweep_pass(int nx, int ny, int nz, const int* per, const T* diag, const T* wx, const T* wy,
+                                const T* wz, const T* b, T* x, int first, int zero, int slab) {
+    g_bad_index = 0;
+    const int S = slab > 0 ? slab : rbp::slab_planes(nx, ny, nz, (int)sizeof(T));
+    const int K = (nz + S - 1) / S;
+    std::vector<int> done(K, 0);
+    for (int j = 0; j < 2 * K; ++j) {
+        int k, pass;
+        rbp::launch_of(K, per[2], j, k, pass);
+        if (pass == 1)
+            for (int dk = -1; dk <= 1; ++dk) {
+                int kk = k + dk;
+                if (kk < 0 || kk >= K) {
+                    if (!per[2]) continue;
+                    kk = (kk + K) % K;
+                }
+                if (!done[kk]) ++g_bad_index;       // a second pass before a neighbouring first pass
+            }
+        if (pass == 0) done[k] = 1;
+        rbp::Pass<T> A;
+        A.nx = nx;
+        A.ny = ny;
+        A.nz = nz;
+        for (int q = 0; q < 3; ++q) A.per[q] = per[q];
+        A.diag = diag;
+        A.wx = wx;
+        A.wy = wy;
+        A.wz = wz;
+        A.b = b;
+        A.x = x;
+        A.colour = pass == 0 ? first : 1 - first;
+        A.zero = pass == 0 && zero;
+        A.z0 = k * S;
+        const int planes = A.z0 + S <= nz ? S : nz - A.z0;
+        int gx, gy, gz;
+        rbp::pass_grid(nx, ny, planes, gx, gy, gz, A.rows);
+        // all threads of a launch read before any writes: the cells a pass sets are never read by it
+        for (int bz = 0; bz < gz; ++bz)
+            for (int by = 0; by < gy; ++by)
+                for (int bx = 0; bx < gx; ++bx)
+                    for (int t = 0; t < rbp::kPairs; ++t) {
+                        int cx, cy, cz;
+                        if (!rbp::pair_cell(A, bx, by, bz, t, cx, cy, cz)) continue;
+                        const long long i = ((long long)cz * ny + cy) * nx + cx;
+                        if (!(i >= 0 && i < (long long)nx * ny * nz)) ++g_bad_index;
+                        x[i] = rbp::cell_value(A, cx, cy, cz);
+                    }
+    }
+    return g_bad_index;
+}
+
+extern "C" {
+long long sweep_pass_host_f64(int nx, int ny, int nz, const int* per, const double* diag, const double* wx,
+                              const double* wy, const double* wz, const double* b, double* x, int first, int zero,
+                              int slab) {
+    return run_sweep_pass<double>(nx, ny, nz, per, diag, wx, wy, wz, b, x, first, zero, slab);
+}
+long long sweep_pass_host_f32(int nx, int ny, int nz, const int* per, const float* diag, const float* wx,
+                              const float* wy, const float* wz, const float* b, float* x, int first, int zero, int slab) {
+    return run_sweep_pass<float>(nx, ny, nz, per, diag, wx, wy, wz, b, x, first, zero, slab);
 }
 }

@@ -201,6 +201,32 @@ def test_queued_in_place_sweep_equals_red_black_gauss_seidel(lib, shape, per, zc
     np.testing.assert_allclose(got, ref0, rtol=tol, atol=tol * np.abs(ref0).max())
 
 
+@pytest.mark.parametrize("slab", [0, 3, 4])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("shape,per,zc", QCASES)
+def test_slab_ordered_passes_equal_red_black_gauss_seidel(lib, shape, per, zc, dtype, slab):
+    """In-place colour passes launched slab by slab (R0, R1, B0, R2, B1, ...; periodic z: B0
+    last), every launch's threads in turn, against the plain sweep's definition; each second pass
+    follows the first passes over its own and the neighbouring slabs; indices in range."""
+    nz, ny, nx = shape
+    rng = np.random.default_rng(13 + sum(shape))
+    diag, *w = _operator(shape, per, rng, dtype)
+    b = rng.standard_normal(shape).astype(dtype)
+    x0 = rng.standard_normal(shape).astype(dtype)
+    tol = 1e-13 if dtype == np.float64 else 2e-6
+    fn = lib.sweep_pass_host_f64 if dtype == np.float64 else lib.sweep_pass_host_f32
+    fn.restype = ctypes.c_longlong
+    arr = lambda a: np.ascontiguousarray(a, dtype=dtype)
+    for first, zero, xin in ((0, 0, x0), (1, 0, x0), (0, 1, np.zeros(shape))):
+        ref = _rbgs_reference(diag, w, b, xin, first)
+        x = np.array(np.full(shape, np.nan) if zero else xin, dtype=dtype, copy=True)
+        args = [arr(diag), *[arr(v) for v in w], arr(b)]
+        bad = fn(nx, ny, nz, (ctypes.c_int * 3)(*per), *[a.ctypes.data_as(ctypes.c_void_p) for a in args],
+                 x.ctypes.data_as(ctypes.c_void_p), first, zero, slab)
+        assert bad == 0
+        np.testing.assert_allclose(x, ref, rtol=tol, atol=tol * np.abs(ref).max())
+
+
 def test_queue_plan(lib):
     """Slabs of 8 planes (all of a thinner grid), chunks of 8192 cells' rows: 256^3 gives 32 slabs
     of 8 planes x 8 row blocks of 32 rows."""
