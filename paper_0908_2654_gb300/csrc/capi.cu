@@ -158,11 +158,11 @@ struct rt_grid {
     double *Xec, *Xnc, *Xet, *Xnt;   // local-elimination sensitivities (current / trial)
     double *He10, *He20, *He1c, *He2c, *He1t, *He2t;   // helium: start, current, trial (n_HeI, n_HeII)
     // CG vectors
-    double *x, *r, *z, *z2, *p, *q;   // z2: second buffer of the FP64 V-cycle's level 0
+    double *x, *r, *z, *p, *q;
     // multigrid
     Hierarchy<float> mgf;
     Hierarchy<double> mgd;
-    float *bf, *xf, *xf2;     // FP32 level-0 right side / solution and its second buffer (mixed)
+    float *bf, *xf;           // FP32 level-0 right side / solution (mixed)
     // reductions
     double *partials, *dots, *scal;
     int* d_err;
@@ -261,11 +261,7 @@ HierarchyStatus build_hierarchy(rt_grid* g, Hierarchy<T>& H, T* diag0, T* wx0, T
     L.wy = wy0;
     L.wz = wz0;
     L.x = nullptr;   // level 0 vectors are bound per solve
-    L.xt = nullptr;
     L.b = nullptr;
-    L.counters = dalloc<unsigned>(1 + 512, ok);
-    H.owned.push_back(L.counters);
-    if (!ok) return HIER_NOMEM;
     H.lv.push_back(L);
     while (d.n() > TailMax<T>::value) {
         if (d.nx % 2 || d.ny % 2 || d.nz % 2) return HIER_ODD;
@@ -280,11 +276,8 @@ HierarchyStatus build_hierarchy(rt_grid* g, Hierarchy<T>& H, T* diag0, T* wx0, T
         c.wy = dalloc<T>(n, ok);
         c.wz = dalloc<T>(n, ok);
         c.x = dalloc<T>(n, ok);
-        c.xt = nullptr;
         c.b = dalloc<T>(n, ok);
-        c.counters = dalloc<unsigned>(1 + 512, ok);
-        for (void* p : {(void*)c.diag, (void*)c.wx, (void*)c.wy, (void*)c.wz, (void*)c.x, (void*)c.b, (void*)c.counters})
-            H.owned.push_back(p);
+        for (void* p : {(void*)c.diag, (void*)c.wx, (void*)c.wy, (void*)c.wz, (void*)c.x, (void*)c.b}) H.owned.push_back(p);
         if (!ok) return HIER_NOMEM;
         H.lv.push_back(c);
     }
@@ -306,24 +299,6 @@ void mg_setup(rt_grid* g, Hierarchy<T>& H) {
     }
 }
 
-// nu red-black Gauss-Seidel sweeps on level L (first colour `first`), each from L.x into L.xt
-// and then swapped; the first sweep starts from a zero iterate (zero) or from L.x plus the
-// prolongated correction of `coarse`
-template <class T>
-void smooth(rt_grid* g, Level<T>& L, int nu, int first, bool zero, const Level<T>* coarse, int cls) {
-    const double n = (double)L.d.n(), t = sizeof(T);
-    for (int k = 0; k < nu; ++k) {
-        const bool z0 = zero && k == 0;
-        const Level<T>* c = k == 0 ? coarse : nullptr;
-        // algorithmic words per cell of a sweep: b, diag, wx, wy, wz and the old iterate read once,
-        // the new iterate written once (no old iterate from zero; the coarse correction adds the
-        // coarse level's x, 1/8 word per fine cell)
-        const double words = (z0 ? 6.0 : 7.0) + (c ? 0.125 : 0.0);
-        run(g, cls, n * words * t, [&] { launch_rbgs_sweep<T>(L, first, z0, c, g->d_err, g->stream); });
-        std::swap(L.x, L.xt);
-    }
-}
-
 // nu red-black Gauss-Seidel sweeps of level L in place (first colour `first`); the first from a
 // zero iterate when `zero`
 template <class T>
@@ -335,7 +310,7 @@ void smooth_inplace(rt_grid* g, Level<T>& L, int nu, int first, bool zero, int c
         // once (no read of x from a zero iterate)
         const double words = z0 ? 6.0 : 7.0;
         int nl = 1;
-        run(g, cls, n * words * t, [&] { nl = launch_rbgs_inplace<T>(L, first, z0, g->d_err, g->stream); });
+        run(g, cls, n * words * t, [&] { nl = launch_rbgs_inplace<T>(L, first, z0, g->stream); });
         g->launches += nl - 1;
     }
 }
@@ -375,17 +350,13 @@ void precondition(rt_grid* g, const double* r) {
         Level<float>& L0 = g->mgf.lv[0];
         L0.b = g->bf;
         L0.x = g->xf;
-        L0.xt = g->xf2;
         vcycle<float>(g, g->mgf);
-        const float* xr = L0.x;
-        run(g, K_CAST, n * 12, [&] { launch_cast_f2d_scaled(g->n, xr, g->z, amax, s); });
+        run(g, K_CAST, n * 12, [&] { launch_cast_f2d_scaled(g->n, g->xf, g->z, amax, s); });
     } else {
         Level<double>& L0 = g->mgd.lv[0];
         L0.b = const_cast<double*>(r);
         L0.x = g->z;
-        L0.xt = g->z2;
         vcycle<double>(g, g->mgd);
-        if (L0.x != g->z) std::swap(g->z, g->z2);   // the result is in the other buffer
     }
 }
 
@@ -393,16 +364,8 @@ int read_scalars(rt_grid* g, int nb, int nslots, double* out, int nmax = 0) {
     run(g, K_FINALIZE, 0.0, [&] { launch_finalize_ext(g->partials, nb, nslots, nmax, g->dots, g->stream); });
     nslots += nmax;
     RT_CUDA(cudaMemcpyAsync(g->h_pinned, g->dots, sizeof(double) * nslots, cudaMemcpyDeviceToHost, g->stream));
-    // the device error word rides along (the multigrid sweeps report there)
-    RT_CUDA(cudaMemcpyAsync(&g->h_pinned[63], g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
     RT_CUDA(cudaStreamSynchronize(g->stream));
     for (int k = 0; k < nslots; ++k) out[k] = g->h_pinned[k];
-    int herr = 0;
-    std::memcpy(&herr, &g->h_pinned[63], sizeof(int));
-    if (herr & 48) {
-        set_detail("a multigrid sweep gave up waiting (%s)", herr & 16 ? "shared-memory copies" : "a colour pass");
-        return RT_ECUDA;
-    }
     return check_launch("reduction");
 }
 
@@ -779,7 +742,7 @@ void rt_destroy_grid(rt_grid* g) {
     if (!g) return;
     cudaSetDevice(g->desc.device);
     double* bufs[] = {g->E0, g->n0, g->src, g->bE, g->wx, g->wy, g->wz, g->Ec, g->nc, g->ecc, g->Et, g->nt, g->ect,
-                      g->step, g->diag, g->rhs, g->wE, g->x, g->r, g->z, g->z2, g->p, g->q, g->partials, g->dots, g->scal,
+                      g->step, g->diag, g->rhs, g->wE, g->x, g->r, g->z, g->p, g->q, g->partials, g->dots, g->scal,
                       g->Xec, g->Xnc, g->Xet, g->Xnt, g->He10, g->He20, g->He1c, g->He2c, g->He1t, g->He2t};
     for (double* b : bufs) cudaFree(b);
     cudaFree(g->wxf);
@@ -787,7 +750,6 @@ void rt_destroy_grid(rt_grid* g) {
     cudaFree(g->wzf);
     cudaFree(g->bf);
     cudaFree(g->xf);
-    cudaFree(g->xf2);
     cudaFree(g->d_err);
     if (g->mgf.lv.size() > 0) cudaFree(g->mgf.lv[0].diag);
     if (g->mgd.lv.size() > 0) cudaFree(g->mgd.lv[0].diag);
@@ -873,7 +835,6 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out) {
         g->wzf = dalloc<float>(n, ok);
         g->bf = dalloc<float>(n, ok);
         g->xf = dalloc<float>(n, ok);
-        g->xf2 = dalloc<float>(n, ok);
         float* diag0 = dalloc<float>(n, ok);
         if (!ok) {
             cudaFree(diag0);
@@ -888,7 +849,6 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out) {
             if (hs == HIER_NOMEM) ok = false;
         }
     } else if (ok) {
-        g->z2 = dalloc<double>(n, ok);
         double* diag0 = dalloc<double>(n, ok);
         if (!ok) {
             cudaFree(diag0);

@@ -193,23 +193,14 @@ struct Level {
     T* wy;
     T* wz;
     T* x;      // current iterate
-    T* xt;     // second iterate buffer: a sweep reads x and writes xt, then the two swap
     T* b;
-    unsigned* counters;   // work counters of the in-place sweep (1 + up to rbq::kMaxPasses / 2)
 };
 template <class T>
 void launch_coarsen(const Level<T>& f, const Level<T>& c, cudaStream_t s);
-// one red-black Gauss-Seidel sweep (first colour `first`) from L.x into L.xt; from a zero iterate
-// (zero_guess) or from L.x plus the prolongation of coarse->x (coarse not null).  Levels whose
-// rows allow it are staged by bulk tensor copies; a CTA that gives up waiting for its copies sets
-// bit 4 of *err (err may be null: then the copies are not used)
+// one red-black Gauss-Seidel sweep of L.x in place as two colour passes (rbpass.cuh), the first
+// from a zero iterate when zero_guess; returns the launches made
 template <class T>
-void launch_rbgs_sweep(const Level<T>& L, int first, bool zero_guess, const Level<T>* coarse, int* err,
-                       cudaStream_t s);
-// one red-black Gauss-Seidel sweep of L.x in place: colour passes launched slab by slab so that
-// the second pass over a slab finds its data in L2 (rbpass.cuh); returns the launches made
-template <class T>
-int launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, int* err, cudaStream_t s);
+int launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, cudaStream_t s);
 // f.x += trilinear prolongation of c.x
 template <class T>
 void launch_prolong_add(const Level<T>& c, const Level<T>& f, cudaStream_t s);

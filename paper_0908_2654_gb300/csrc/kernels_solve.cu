@@ -16,16 +16,7 @@
 //        coefficients);
 //      - a single-CTA solver that runs the remaining coarse levels in shared memory and finishes
 //        with a dense Cholesky solve (or the exact 1-cell solve) on the coarsest one.
-#include <cuda.h>
-
-#include <map>
-#include <mutex>
-#include <tuple>
-
 #include "kernels.cuh"
-#include "smoother.cuh"
-#include "smoother_tma.cuh"
-#include "rbqueue.cuh"
 #include "rbpass.cuh"
 
 namespace {
@@ -259,216 +250,6 @@ __global__ void k_cg_scalars(double* scal, const double* dots, int phase) {
 
 // ------------------------------------------------------------------- multigrid kernels
 
-template <class T>
-__global__ void __launch_bounds__(sweep::kThreads) k_rbgs_sweep(sweep::Args<T> A) {
-    extern __shared__ __align__(16) unsigned char smem_sweep[];
-    sweep::Tile<T>& S = *reinterpret_cast<sweep::Tile<T>*>(smem_sweep);
-    const long long nit = sweep::items(A.d, A.zc);
-    for (long long it = blockIdx.x; it < nit; it += gridDim.x) {
-        sweep::Item I;
-        sweep::item_setup(A, it, threadIdx.x, I);
-        // plane p is staged, the first colour computed one plane behind it and the second colour
-        // two planes behind (it needs the first colour on both of its z neighbours); the loads of
-        // plane p + 1 are in flight while plane p's colours are computed
-        sweep::Fetch<T> F;
-        sweep::fetch(A, I, I.z0 - 2, F);
-        for (int p = I.z0 - 2; p <= I.z1 + 1; ++p) {
-            sweep::stage(S, p, threadIdx.x, F);
-            if (p < I.z1 + 1) sweep::fetch(A, I, p + 1, F);
-            __syncthreads();
-            if (p - 1 >= I.z0 - 1) sweep::first_colour(A, S, I, p - 1);
-            __syncthreads();
-            if (p - 2 >= I.z0) sweep::second_colour(A, S, I, p - 2);
-            __syncthreads();
-        }
-    }
-}
-
-// ---- TMA-fed sweep (smoother_tma.cuh): bulk tensor copies, mbarriers with bounded waits
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    unsigned long long state;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                 : "=l"(state)
-                 : "r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-    (void)state;
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
-    unsigned long long state;
-    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(bar)) : "memory");
-    (void)state;
-}
-// tries to see the phase with the given parity complete at most `limit` times (each try may
-// suspend the thread for a short, hardware-defined time); false when it never did
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit) {
-    const unsigned a = smem_u32(bar);
-    for (long long k = 0; k < limit; ++k) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
-                                            unsigned long long* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
-            smem_u32(dst)),
-        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
-}
-
-constexpr long long kWaitTries = 1LL << 21;
-
-template <class T>
-__global__ void __launch_bounds__(tsweep::kThreads) k_rbgs_sweep_tma(tsweep::Args<T> A, const __grid_constant__ CUtensorMap mb,
-                                                                  const __grid_constant__ CUtensorMap md,
-                                                                  const __grid_constant__ CUtensorMap mwx,
-                                                                  const __grid_constant__ CUtensorMap mwy,
-                                                                  const __grid_constant__ CUtensorMap mwz,
-                                                                  const __grid_constant__ CUtensorMap mx) {
-    using G = tsweep::Geom<T>;
-    extern __shared__ __align__(128) unsigned char smem_tsweep[];
-    tsweep::Tile<T>& S = *reinterpret_cast<tsweep::Tile<T>*>(smem_tsweep);
-    __shared__ int fail;
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        for (int s = 0; s < G::NR; ++s) mbar_init(&S.bar[s], 1);
-        fail = 0;
-    }
-    __syncthreads();
-    const CUtensorMap* maps[tsweep::NARR] = {&mb, &md, &mwx, &mwy, &mwz, &mx};
-    constexpr unsigned tile_bytes = G::TILE * sizeof(T);
-    const int na = A.zero_guess ? tsweep::NARR - 1 : tsweep::NARR;   // no copy of a zero iterate
-    long long seq = 0;   // sequence number of the next plane this CTA consumes
-    const long long nit = sweep::items(A.d, A.zc);
-    for (long long it = blockIdx.x; it < nit; it += gridDim.x) {
-        tsweep::Item I;
-        tsweep::item_setup(A, it, tid, I);
-        const int p0 = I.z0 - 2, p1 = I.z1 + 1;
-        // thread 0: copies of plane p into its slot (a plane outside a non-periodic grid is not
-        // copied; its barrier phase is completed by a plain arrival)
-        auto issue = [&](int p, long long sq) {
-            const int s = tsweep::slot_of(sq, G::NR);
-            const int gz = sweep::gcoord(p, A.d.nz, A.d.per[2]);
-            if (gz < 0) {
-                mbar_arrive(&S.bar[s]);
-                return;
-            }
-            fence_proxy_async();   // the slot's earlier generic reads and writes come first
-            mbar_expect_tx(&S.bar[s], na * tile_bytes);
-#pragma unroll
-            for (int a = 0; a < tsweep::NARR; ++a)
-                if (a < na) tma_load_3d(S.t[s][a], maps[a], I.X0 - G::XOFF, I.Y0 - tsweep::HALO, gz, &S.bar[s]);
-        };
-        if (tid == 0)
-            for (int p = p0; p < p0 + G::D && p <= p1; ++p) issue(p, seq + (p - p0));
-        for (int p = p0; p <= p1; ++p) {
-            const long long sq = seq + (p - p0);
-            if (tid == 0 && p + G::D <= p1) issue(p + G::D, sq + G::D);
-            const int s = tsweep::slot_of(sq, G::NR);
-            if (!mbar_wait(&S.bar[s], (unsigned)((sq / G::NR) & 1), kWaitTries)) fail = 1;
-            tsweep::fix_plane(A, S, I, p, s, tid, blockDim.x);
-            __syncthreads();
-            if (fail) {
-                // give up: wait (bounded) for this CTA's copies still in flight, record, return
-                if (tid == 0) {
-                    const int last = p + G::D <= p1 ? p + G::D : p1;
-                    for (int q = p + 1; q <= last; ++q) {
-                        const long long sq2 = seq + (q - p0);
-                        mbar_wait(&S.bar[tsweep::slot_of(sq2, G::NR)], (unsigned)((sq2 / G::NR) & 1), kWaitTries);
-                    }
-                    atomicOr(A.err, 16);
-                }
-                return;
-            }
-            if (p - 1 >= p0 + 1) tsweep::first_colour(A, S, I, p - 1, sq - 1);
-            __syncthreads();
-            if (p - 2 >= I.z0) tsweep::second_colour(A, S, I, p - 2, sq - 2);
-            __syncthreads();
-        }
-        seq += p1 - p0 + 1;
-    }
-}
-
-// ---- in-place red-black sweep as two colour passes ordered for L2 reuse (rbqueue.cuh)
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-constexpr long long kQueueWaitTries = 1LL << 24;
-
-template <class T>
-__global__ void __launch_bounds__(rbq::kThreads) k_rbgs_queue(rbq::Args<T> A) {
-    __shared__ unsigned next_item;
-    __shared__ int give_up;
-    const rbq::Plan& P = A.P;
-    const unsigned nitems = 2u * (unsigned)P.nslab * (unsigned)P.chunks;
-    const unsigned complete = (unsigned)P.chunks * (rbq::kThreads / 32);   // warps that finish a pass
-    const int tid = threadIdx.x;
-    // x changes during the kernel: read it from L2, never from a stale L1 line
-    auto ld = [&](long long j) { return __ldcg(A.x + j); };
-    if (tid == 0) next_item = atomicAdd(A.next, 1u);
-    __syncthreads();
-    unsigned s = next_item;
-    for (;;) {
-        __syncthreads();                                   // every thread has read next_item
-        if (tid == 0) next_item = atomicAdd(A.next, 1u);   // the following item, fetched meanwhile
-        if (s >= nitems) break;
-        int k, pass;
-        rbq::pass_of(P, (int)(s / (unsigned)P.chunks), k, pass);
-        const int c = (int)(s % (unsigned)P.chunks);
-        if (pass == 1) {
-            // the first passes over slabs k - 1, k and k + 1 must be complete
-            if (tid == 0) {
-                give_up = 0;
-                for (int dk = -1; dk <= 1 && !give_up; ++dk) {
-                    int kk = k + dk;
-                    if (kk < 0 || kk >= P.nslab) {
-                        if (!P.per[2]) continue;
-                        kk = (kk + P.nslab) % P.nslab;
-                    }
-                    long long tries = 0;
-                    while (ld_acquire(A.done + kk) < complete) {
-                        if (++tries > kQueueWaitTries) {
-                            give_up = 1;
-                            break;
-                        }
-                        __nanosleep(100);
-                    }
-                }
-                if (give_up) atomicOr(A.err, 32);
-            }
-            __syncthreads();
-            if (!give_up) rbq::chunk_pass(A, k, c, pass, tid, blockDim.x, ld);
-        } else {
-            rbq::chunk_pass(A, k, c, pass, tid, blockDim.x, ld);
-            // each warp signals its part of the chunk once its stores are visible
-            __syncwarp();
-            if ((tid & 31) == 0) {
-                __threadfence();
-                atomicAdd(A.done + k, 1u);
-            }
-        }
-        __syncthreads();                                   // next_item has been written
-        s = next_item;
-    }
-}
-
 // one colour pass of a red-black sweep over planes [z0, z0 + gridDim.z) in place (rbpass.cuh)
 template <class T>
 __global__ void __launch_bounds__(rbp::kPairs) k_rbgs_pass(rbp::Pass<T> A) {
@@ -483,17 +264,11 @@ __global__ void __launch_bounds__(kBlock) k_prolong_add(Level<T> c, Level<T> f) 
     const Dims fd = f.d;
     const int nxy = fd.nx * fd.ny;
     const long long n = fd.n();
-    sweep::Args<T> A;
-    A.xc = c.x;
-    A.cd.nx = c.d.nx;
-    A.cd.ny = c.d.ny;
-    A.cd.nz = c.d.nz;
-    for (int k = 0; k < 3; ++k) A.cd.per[k] = c.d.per[k];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int z = (int)(i / nxy);
         const int r = (int)(i - (long long)z * nxy);
         const int y = r / fd.nx, x = r - y * fd.nx;
-        f.x[i] += sweep::prolong_at(A, x, y, z);
+        f.x[i] += rbp::prolong_at(c.x, c.d.nx, c.d.ny, c.d.nz, c.d.per, x, y, z);
     }
 }
 
@@ -883,132 +658,11 @@ template <class T>
 void launch_coarsen(const Level<T>& f, const Level<T>& c, cudaStream_t s) {
     k_coarsen<T><<<grid_for(c.d.n()), kBlock, 0, s>>>(f, c);
 }
-namespace {
-sweep::Geo geo_of(const Dims& d) {
-    sweep::Geo g;
-    g.nx = d.nx;
-    g.ny = d.ny;
-    g.nz = d.nz;
-    for (int k = 0; k < 3; ++k) g.per[k] = d.per[k];
-    return g;
-}
-int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
-            n = 152;
-    }
-    return n;
-}
-}  // namespace
 
-// ---- tensor maps of the TMA-fed sweep
-
-using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// the driver's tensor-map encoder, looked up once through the runtime (null if unavailable)
-EncodeTiled encoder() {
-    static EncodeTiled fn = nullptr;
-    static bool tried = false;
-    static std::mutex mu;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!tried) {
-        tried = true;
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiled>(p);
-    }
-    return fn;
-}
-
-// The tensor map of one level array for the sweep's box (cached per address and shape: the
-// level arrays live as long as their grid).  False if it cannot be encoded.
 template <class T>
-bool sweep_map(const T* base, const Dims& d, CUtensorMap* out) {
-    using G = tsweep::Geom<T>;
-    static std::mutex mu;
-    static std::map<std::tuple<const void*, int, int, int>, CUtensorMap> cache;
-    std::lock_guard<std::mutex> lock(mu);
-    const auto key = std::make_tuple((const void*)base, d.nx, d.ny, d.nz);
-    auto it = cache.find(key);
-    if (it != cache.end()) {
-        *out = it->second;
-        return true;
-    }
-    EncodeTiled enc = encoder();
-    if (!enc) return false;
-    CUtensorMap m;
-    const cuuint64_t dim[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
-    const cuuint64_t stride[2] = {(cuuint64_t)d.nx * sizeof(T), (cuuint64_t)d.nx * d.ny * sizeof(T)};
-    const cuuint32_t box[3] = {(cuuint32_t)G::BX, (cuuint32_t)G::BY, 1};
-    const cuuint32_t estride[3] = {1, 1, 1};
-    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-    if (enc(&m, dt, 3, const_cast<T*>(base), dim, stride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return false;
-    cache[key] = m;
-    *out = m;
-    return true;
-}
-
-// The TMA-fed sweep when the level allows it: no fused coarse correction, rows a multiple of
-// 16 bytes (the tensor's strides) and every array 16-byte aligned.  False when not launched.
-template <class T>
-bool launch_sweep_tma(const Level<T>& L, int first, bool zero_guess, int* err, cudaStream_t s) {
+int launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, cudaStream_t s) {
     const Dims& d = L.d;
-    if ((d.nx * sizeof(T)) % 16 != 0) return false;
-    const T* arrs[6] = {L.b, L.diag, L.wx, L.wy, L.wz, L.x};
-    for (const T* a : arrs)
-        if (!a || (reinterpret_cast<uintptr_t>(a) % 16) != 0) return false;
-    CUtensorMap m[6];
-    for (int a = 0; a < 6; ++a)
-        if (!sweep_map<T>(arrs[a], d, &m[a])) return false;
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        cudaFuncSetAttribute(k_rbgs_sweep_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(tsweep::Tile<T>));
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbgs_sweep_tma<T>, tsweep::kThreads,
-                                                          sizeof(tsweep::Tile<T>)) != cudaSuccess ||
-            per_sm < 1)
-            per_sm = 1;
-    }
-    tsweep::Args<T> A;
-    A.d = geo_of(d);
-    A.b = L.b;
-    A.diag = L.diag;
-    A.wx = L.wx;
-    A.wy = L.wy;
-    A.wz = L.wz;
-    A.xin = L.x;
-    A.xout = L.xt;
-    A.first = first;
-    A.zero_guess = zero_guess ? 1 : 0;
-    const long long slots = (long long)sm_count() * per_sm;
-    A.zc = sweep::chunk_planes(A.d, slots);
-    A.err = err;
-    const long long nit = sweep::items(A.d, A.zc);
-    const int grid = (int)(nit < slots ? nit : slots);
-    k_rbgs_sweep_tma<T><<<grid, tsweep::kThreads, sizeof(tsweep::Tile<T>), s>>>(A, m[0], m[1], m[2], m[3], m[4], m[5]);
-    return true;
-}
-
-template <class T>
-int launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, int* err, cudaStream_t s) {
-    (void)err;
-    const Dims& d = L.d;
-    const int S = rbp::slab_planes(d.nx, d.ny, d.nz, (int)sizeof(T));
-    const int K = (d.nz + S - 1) / S;
-    for (int j = 0; j < 2 * K; ++j) {
-        int slab, pass;
-        rbp::launch_of(K, d.per[2], j, slab, pass);
+    for (int pass = 0; pass < 2; ++pass) {
         rbp::Pass<T> A;
         A.nx = d.nx;
         A.ny = d.ny;
@@ -1022,13 +676,14 @@ int launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, int* err,
         A.x = L.x;
         A.colour = pass == 0 ? first : 1 - first;
         A.zero = pass == 0 && zero_guess;
-        A.z0 = slab * S;
-        const int planes = A.z0 + S <= d.nz ? S : d.nz - A.z0;
+        A.z0 = 0;
+        A.planes = d.nz;
+        A.rev = pass;   // the second pass starts on the planes the first read last
         int gx, gy, gz;
-        rbp::pass_grid(d.nx, d.ny, planes, gx, gy, gz, A.rows);
+        rbp::pass_grid(d.nx, d.ny, d.nz, gx, gy, gz, A.rows);
         k_rbgs_pass<T><<<dim3(gx, gy, gz), rbp::kPairs, 0, s>>>(A);
     }
-    return 2 * K;
+    return 2;
 }
 
 template <class T>
@@ -1036,38 +691,6 @@ void launch_prolong_add(const Level<T>& c, const Level<T>& f, cudaStream_t s) {
     k_prolong_add<T><<<grid_for(f.d.n()), kBlock, 0, s>>>(c, f);
 }
 
-template <class T>
-void launch_rbgs_sweep(const Level<T>& L, int first, bool zero_guess, const Level<T>* coarse, int* err,
-                       cudaStream_t s) {
-    if (!coarse && err && launch_sweep_tma<T>(L, first, zero_guess, err, s)) return;
-    // resident CTAs per SM of the sweep kernel (shared memory bound), found once per precision
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        cudaFuncSetAttribute(k_rbgs_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(sweep::Tile<T>));
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbgs_sweep<T>, sweep::kThreads,
-                                                          sizeof(sweep::Tile<T>)) != cudaSuccess ||
-            per_sm < 1)
-            per_sm = 1;
-    }
-    sweep::Args<T> A;
-    A.d = geo_of(L.d);
-    A.diag = L.diag;
-    A.wx = L.wx;
-    A.wy = L.wy;
-    A.wz = L.wz;
-    A.b = L.b;
-    A.xin = L.x;
-    A.xout = L.xt;
-    A.first = first;
-    A.zero_guess = zero_guess ? 1 : 0;
-    const long long slots = (long long)sm_count() * per_sm;
-    A.zc = sweep::chunk_planes(A.d, slots);
-    A.xc = coarse ? coarse->x : nullptr;
-    A.cd = coarse ? geo_of(coarse->d) : A.d;
-    const long long nit = sweep::items(A.d, A.zc);
-    const int grid = (int)(nit < slots ? nit : slots);
-    k_rbgs_sweep<T><<<grid, sweep::kThreads, sizeof(sweep::Tile<T>), s>>>(A);
-}
 template <class T>
 void launch_resid_restrict(const Level<T>& f, const Level<T>& c, cudaStream_t s) {
     k_resid_restrict<T><<<grid_for(c.d.n()), kBlock, 0, s>>>(f, c);
@@ -1100,12 +723,10 @@ int launch_tail(const Level<T>& L, int ncycles, int nu, cudaStream_t s) {
 
 template void launch_coarsen<float>(const Level<float>&, const Level<float>&, cudaStream_t);
 template void launch_coarsen<double>(const Level<double>&, const Level<double>&, cudaStream_t);
-template void launch_rbgs_sweep<float>(const Level<float>&, int, bool, const Level<float>*, int*, cudaStream_t);
-template int launch_rbgs_inplace<float>(const Level<float>&, int, bool, int*, cudaStream_t);
-template int launch_rbgs_inplace<double>(const Level<double>&, int, bool, int*, cudaStream_t);
+template int launch_rbgs_inplace<float>(const Level<float>&, int, bool, cudaStream_t);
+template int launch_rbgs_inplace<double>(const Level<double>&, int, bool, cudaStream_t);
 template void launch_prolong_add<float>(const Level<float>&, const Level<float>&, cudaStream_t);
 template void launch_prolong_add<double>(const Level<double>&, const Level<double>&, cudaStream_t);
-template void launch_rbgs_sweep<double>(const Level<double>&, int, bool, const Level<double>*, int*, cudaStream_t);
 template void launch_resid_restrict<float>(const Level<float>&, const Level<float>&, cudaStream_t);
 template void launch_resid_restrict<double>(const Level<double>&, const Level<double>&, cudaStream_t);
 template int launch_tail<float>(const Level<float>&, int, int, cudaStream_t);

@@ -1,22 +1,19 @@
-// Red-black Gauss-Seidel sweeps of a multigrid level as in-place colour passes, launched slab by
-// slab so that the second pass over a slab finds the slab's arrays in L2.
+// Red-black Gauss-Seidel sweeps of a multigrid level as two in-place colour passes, and the
+// trilinear prolongation of a coarse correction.
 //
 // The level's operator is (S x)_i = diag_i x_i - sum_faces w_f x_nb (w on each cell's +x/+y/+z
 // face, zero on boundary faces).  A sweep sets every cell of the first colour (parity of x + y + z
 // equal to `first`) from its neighbours, which all have the other colour, then every cell of the
 // other colour from the new first-colour values, both in place.
 //
-// A pass over the planes [z0, z1) is one kernel launch with one thread per pair of x-neighbours
-// (one cell of each colour), a block per row segment and plane, and no loop, barrier or
-// division.  Levels larger than a slab of planes are swept in the launch order
-//     R0, R1, B0, R2, B1, ..., R(K-1), B(K-2), B(K-1)        (periodic z: B0 moved to the end)
-// where Rk / Bk is the first / second colour pass over slab k: the second pass over slab k runs
-// after the first passes over slabs k - 1, k and k + 1 (the stream orders launches), and right
-// after the first pass over slab k + 1, while the slab's arrays are still in L2.  One sweep then
-// moves about 7 words per cell through HBM (b, diag, wx, wy, wz and x read, x written).
+// A pass is one kernel launch with one thread per pair of x-neighbours (one cell of each colour),
+// a block per row segment and plane, and no loop, barrier or division: all SM resources go to
+// keeping loads in flight.  The second pass takes the planes in reverse order, so that it starts
+// on the planes the first pass read last (still in L2), and the next sweep's first pass starts on
+// the planes this second pass read last.
 //
-// The functions are host/device so that a host build can run the passes in the same order and
-// compare them with a plain sweep (tests/host/smoother_host.cu).
+// The functions are host/device so that a host build can run the passes and compare them with a
+// plain sweep (tests/host/smoother_host.cu).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -44,6 +41,8 @@ struct Pass {
     int colour;     // parity of the cells this pass sets
     int zero;       // the old iterate is zero (first pass of a sweep from zero)
     int z0;         // first plane of the pass
+    int planes;     // planes of the pass
+    int rev;        // blocks take the planes from the last to the first
     int rows;       // rows per block: kPairs / pairs per row (at least 1)
 };
 
@@ -61,7 +60,7 @@ RT_HD bool pair_cell(const Pass<T>& A, int bx, int by, int bz, int t, int& x, in
         px = t - ry * hp;
     }
     y = by * A.rows + ry;
-    z = A.z0 + bz;
+    z = A.z0 + (A.rev ? A.planes - 1 - bz : bz);
     if (px >= hp || y >= A.ny || ry >= A.rows) return false;
     x = 2 * px + ((y + z + A.colour) & 1);   // the pair's cell of this colour
     return x < A.nx;
@@ -106,47 +105,30 @@ inline void pass_grid(int nx, int ny, int planes, int& gx, int& gy, int& gz, int
     gz = planes;
 }
 
-// slabs of a level: planes per slab so that a slab of the seven arrays stays well inside L2
-// (about 40 MB); a level that fits is one slab
-inline int slab_planes(int nx, int ny, int nz, int bytes_per_value, double l2_budget = 40e6) {
-    const double plane = 7.0 * bytes_per_value * (double)nx * ny;
-    int s = (int)(l2_budget / plane);
-    if (s < 2) s = 2;
-    if (s >= nz) return nz;
-    return s;
-}
-
-// launch j of a sweep with K slabs -> (slab, colour pass: 0 first, 1 second); 2K launches
-inline void launch_of(int K, int per_z, int j, int& slab, int& pass) {
-    if (j == 0) {
-        slab = 0;
-        pass = 0;
-        return;
-    }
-    if (j == 2 * K - 1) {
-        slab = per_z ? 0 : K - 1;
-        pass = 1;
-        return;
-    }
-    if (!per_z) {
-        const int m = j - 1;
-        slab = (m % 2 == 0) ? m / 2 + 1 : (m - 1) / 2;
-        pass = m % 2;
-        return;
-    }
-    if (j == 1) {
-        slab = 1;
-        pass = 0;
-        return;
-    }
-    if (j == 2 * K - 2) {
-        slab = K - 1;
-        pass = 1;
-        return;
-    }
-    const int m = j - 2;
-    slab = (m % 2 == 0) ? m / 2 + 2 : (m - 1) / 2 + 1;
-    pass = m % 2;
+// coarse-cell value of the trilinear cell-centred prolongation at fine cell (x, y, z): weights
+// 3/4 and 1/4 along each axis from the coarse cell holding the fine cell and its neighbour on the
+// fine cell's side (the cell itself at a non-periodic edge)
+template <class T>
+RT_HD T prolong_at(const T* xc, int cnx, int cny, int cnz, const int* per, int x, int y, int z) {
+    const int X = x >> 1, Y = y >> 1, Z = z >> 1;
+    auto other = [](int C, int odd, int n, int p) {
+        const int c = odd ? C + 1 : C - 1;
+        if (c >= 0 && c < n) return c;
+        return p ? (c + n) % n : C;
+    };
+    const int X2 = other(X, x & 1, cnx, per[0]);
+    const int Y2 = other(Y, y & 1, cny, per[1]);
+    const int Z2 = other(Z, z & 1, cnz, per[2]);
+    const long long sy = cnx, sz = (long long)cnx * cny;
+    auto C = [&](int a, int b, int e) {
+        const long long j = (long long)e * sz + (long long)b * sy + a;
+        RT_SWEEP_CHECK(j >= 0 && j < sz * cnz);
+        return xc[j];
+    };
+    const T w1 = T(0.75), w2 = T(0.25);
+    const T v1 = w1 * (w1 * C(X, Y, Z) + w2 * C(X2, Y, Z)) + w2 * (w1 * C(X, Y2, Z) + w2 * C(X2, Y2, Z));
+    const T v2 = w1 * (w1 * C(X, Y, Z2) + w2 * C(X2, Y, Z2)) + w2 * (w1 * C(X, Y2, Z2) + w2 * C(X2, Y2, Z2));
+    return w1 * v1 + w2 * v2;
 }
 
 }  // namespace rbp

@@ -1,10 +1,10 @@
-"""The fused red-black Gauss-Seidel sweep of the multigrid levels (smoother.cuh), compiled for
-the host and run CTA by CTA in the order its barriers impose, against a plain red-black
-Gauss-Seidel sweep written from its definition: update every cell of the first colour from its
-neighbours' old values, x_i = (b_i + sum_faces w_f x_nb) / diag_i, then every cell of the other
-colour from the new values.  Also: the fused coarse-grid correction (old iterate plus the
-trilinear cell-centred prolongation of a coarse vector), the zero start, every global index in
-range, several z chunks and tiles cut by the grid's edge, periodic and reflecting axes."""
+"""The red-black Gauss-Seidel sweep of the multigrid levels (rbpass.cuh), compiled for the host
+and run launch by launch, block by block, against a plain red-black Gauss-Seidel sweep written
+from its definition: update every cell of the first colour from its neighbours' old values,
+x_i = (b_i + sum_faces w_f x_nb) / diag_i, then every cell of the other colour from the new
+values.  Also: the zero start, each pass setting exactly the cells of its colour, every global
+index in range, rows shorter and longer than a block, periodic and reflecting axes, odd
+non-periodic dimensions; and the trilinear cell-centred prolongation of a coarse vector."""
 import ctypes
 import os
 import shutil
@@ -87,175 +87,49 @@ def _prolong_reference(xc, fshape, per):
     return out
 
 
-def _call_tma(lib, dtype, shape, per, diag, w, b, xin, first, zero, zc, grid=5):
-    nz, ny, nx = shape
-    fn = lib.sweep_tma_host_f64 if dtype == np.float64 else lib.sweep_tma_host_f32
-    fn.restype = ctypes.c_longlong
-    arr = lambda a: np.ascontiguousarray(a, dtype=dtype)
-    args = [arr(diag), *[arr(v) for v in w], arr(b), arr(xin)]
-    out = np.full(shape, np.nan, dtype=dtype)
-    perc = (ctypes.c_int * 3)(*per)
-    bad = fn(nx, ny, nz, perc, *[a.ctypes.data_as(ctypes.c_void_p) for a in args], out.ctypes.data_as(ctypes.c_void_p),
-             first, zero, zc, grid)
-    return out, bad
-
-
-def _call_queue(lib, dtype, shape, per, diag, w, b, xin, first, zero):
-    nz, ny, nx = shape
-    fn = lib.sweep_queue_host_f64 if dtype == np.float64 else lib.sweep_queue_host_f32
-    fn.restype = ctypes.c_longlong
-    arr = lambda a: np.ascontiguousarray(a, dtype=dtype)
-    args = [arr(diag), *[arr(v) for v in w], arr(b)]
-    x = np.array(xin, dtype=dtype, copy=True)
-    perc = (ctypes.c_int * 3)(*per)
-    bad = fn(nx, ny, nz, perc, *[a.ctypes.data_as(ctypes.c_void_p) for a in args], x.ctypes.data_as(ctypes.c_void_p),
-             first, zero)
-    return x, bad
-
-
-def _call(lib, dtype, shape, per, diag, w, b, xin, first, zero, zc, xc=None, nth=256, grid=7):
+def _sweep(lib, dtype, shape, per, diag, w, b, xin, first, zero):
     nz, ny, nx = shape
     fn = lib.sweep_host_f64 if dtype == np.float64 else lib.sweep_host_f32
     fn.restype = ctypes.c_longlong
     arr = lambda a: np.ascontiguousarray(a, dtype=dtype)
-    args = [arr(diag), *[arr(v) for v in w], arr(b), arr(xin)]
-    out = np.full(shape, np.nan, dtype=dtype)
-    perc = (ctypes.c_int * 3)(*per)
-    cshape = xc.shape if xc is not None else (1, 1, 1)
-    xcp = arr(xc).ctypes.data_as(ctypes.c_void_p) if xc is not None else None
-    bad = fn(nx, ny, nz, perc, *[a.ctypes.data_as(ctypes.c_void_p) for a in args], out.ctypes.data_as(ctypes.c_void_p),
-             first, zero, zc, xcp, cshape[2], cshape[1], cshape[0], nth, grid)
-    return out, bad
+    args = [arr(diag), *[arr(v) for v in w], arr(b)]
+    x = np.array(xin, dtype=dtype, copy=True)
+    bad = fn(nx, ny, nz, (ctypes.c_int * 3)(*per), *[a.ctypes.data_as(ctypes.c_void_p) for a in args],
+             x.ctypes.data_as(ctypes.c_void_p), first, zero)
+    return x, bad
 
 
-CASES = [((20, 32, 64), (True, True, True), 4), ((24, 40, 40), (False, False, False), 0),
-         ((4, 6, 8), (False, True, False), 0), ((10, 18, 36), (True, False, True), 3),
-         ((12, 20, 34), (False, False, True), 5), ((8, 8, 8), (True, True, True), 0)]
-
-
-@pytest.mark.parametrize("dtype", [np.float64, np.float32])
-@pytest.mark.parametrize("shape,per,zc", CASES)
-def test_fused_sweep_equals_red_black_gauss_seidel(lib, shape, per, zc, dtype):
-    rng = np.random.default_rng(sum(shape))
-    diag, *w = _operator(shape, per, rng, dtype)
-    b = rng.standard_normal(shape).astype(dtype)
-    x0 = rng.standard_normal(shape).astype(dtype)
-    tol = 1e-13 if dtype == np.float64 else 2e-6
-    for first in (0, 1):
-        ref = _rbgs_reference(diag, w, b, x0, first)
-        got, bad = _call(lib, dtype, shape, per, diag, w, b, x0, first, 0, zc, grid=1 if first else 7)
-        assert bad == 0
-        np.testing.assert_allclose(got, ref, rtol=tol, atol=tol * np.abs(ref).max())
-    ref0 = _rbgs_reference(diag, w, b, np.zeros(shape), 0)
-    got, bad = _call(lib, dtype, shape, per, diag, w, b, np.full(shape, np.nan), 0, 1, zc)
-    assert bad == 0
-    np.testing.assert_allclose(got, ref0, rtol=tol, atol=tol * np.abs(ref0).max())
+CASES = [((20, 32, 64), (True, True, True)), ((24, 40, 40), (False, False, False)),
+         ((4, 6, 8), (False, True, False)), ((10, 18, 36), (True, False, True)),
+         ((12, 20, 34), (False, False, True)), ((8, 8, 8), (True, True, True)),
+         ((6, 4, 300), (True, False, False)), ((37, 8, 10), (False, True, False)),
+         ((24, 6, 8), (True, True, False))]
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
-@pytest.mark.parametrize("shape,per,zc", CASES)
-def test_tensor_copy_sweep_equals_red_black_gauss_seidel(lib, shape, per, zc, dtype):
-    """The sweep fed by bulk tensor copies (boxes with zeros outside the grid, wrapped edges of
-    periodic axes patched, planes copied ahead into a ring of slots), its copies emulated in the
-    kernel's order, against the plain sweep's definition."""
-    rng = np.random.default_rng(3 + sum(shape))
-    diag, *w = _operator(shape, per, rng, dtype)
-    b = rng.standard_normal(shape).astype(dtype)
-    x0 = rng.standard_normal(shape).astype(dtype)
-    tol = 1e-13 if dtype == np.float64 else 2e-6
-    for first in (0, 1):
-        ref = _rbgs_reference(diag, w, b, x0, first)
-        got, bad = _call_tma(lib, dtype, shape, per, diag, w, b, x0, first, 0, zc, grid=1 if first else 5)
-        assert bad == 0
-        np.testing.assert_allclose(got, ref, rtol=tol, atol=tol * np.abs(ref).max())
-    ref0 = _rbgs_reference(diag, w, b, np.zeros(shape), 1)
-    got, bad = _call_tma(lib, dtype, shape, per, diag, w, b, np.full(shape, np.nan), 1, 1, zc)
-    assert bad == 0
-    np.testing.assert_allclose(got, ref0, rtol=tol, atol=tol * np.abs(ref0).max())
-
-
-QCASES = CASES + [((40, 16, 16), (True, False, True), 0), ((37, 8, 10), (False, True, False), 0),
-                  ((24, 6, 8), (True, True, False), 0)]
-
-
-@pytest.mark.parametrize("dtype", [np.float64, np.float32])
-@pytest.mark.parametrize("shape,per,zc", QCASES)
-def test_queued_in_place_sweep_equals_red_black_gauss_seidel(lib, shape, per, zc, dtype):
-    """The in-place sweep whose two colour passes are cut into slab chunks and queued (R0, R1,
-    B0, R2, B1, ...; periodic z: B0 last), run item by item in queue order, against the plain
-    sweep's definition; every second-pass chunk finds the first passes over its own and the
-    neighbouring slabs complete, and every index lies in the grid (odd nz too)."""
-    rng = np.random.default_rng(11 + sum(shape))
-    diag, *w = _operator(shape, per, rng, dtype)
-    b = rng.standard_normal(shape).astype(dtype)
-    x0 = rng.standard_normal(shape).astype(dtype)
-    tol = 1e-13 if dtype == np.float64 else 2e-6
-    for first in (0, 1):
-        ref = _rbgs_reference(diag, w, b, x0, first)
-        got, bad = _call_queue(lib, dtype, shape, per, diag, w, b, x0, first, 0)
-        assert bad == 0
-        np.testing.assert_allclose(got, ref, rtol=tol, atol=tol * np.abs(ref).max())
-    ref0 = _rbgs_reference(diag, w, b, np.zeros(shape), 0)
-    got, bad = _call_queue(lib, dtype, shape, per, diag, w, b, np.full(shape, np.nan), 0, 1)
-    assert bad == 0
-    np.testing.assert_allclose(got, ref0, rtol=tol, atol=tol * np.abs(ref0).max())
-
-
-@pytest.mark.parametrize("slab", [0, 3, 4])
-@pytest.mark.parametrize("dtype", [np.float64, np.float32])
-@pytest.mark.parametrize("shape,per,zc", QCASES)
-def test_slab_ordered_passes_equal_red_black_gauss_seidel(lib, shape, per, zc, dtype, slab):
-    """In-place colour passes launched slab by slab (R0, R1, B0, R2, B1, ...; periodic z: B0
-    last), every launch's threads in turn, against the plain sweep's definition; each second pass
-    follows the first passes over its own and the neighbouring slabs; indices in range."""
-    nz, ny, nx = shape
+@pytest.mark.parametrize("shape,per", CASES)
+def test_sweep_equals_red_black_gauss_seidel(lib, shape, per, dtype):
     rng = np.random.default_rng(13 + sum(shape))
     diag, *w = _operator(shape, per, rng, dtype)
     b = rng.standard_normal(shape).astype(dtype)
     x0 = rng.standard_normal(shape).astype(dtype)
     tol = 1e-13 if dtype == np.float64 else 2e-6
-    fn = lib.sweep_pass_host_f64 if dtype == np.float64 else lib.sweep_pass_host_f32
-    fn.restype = ctypes.c_longlong
-    arr = lambda a: np.ascontiguousarray(a, dtype=dtype)
     for first, zero, xin in ((0, 0, x0), (1, 0, x0), (0, 1, np.zeros(shape))):
         ref = _rbgs_reference(diag, w, b, xin, first)
-        x = np.array(np.full(shape, np.nan) if zero else xin, dtype=dtype, copy=True)
-        args = [arr(diag), *[arr(v) for v in w], arr(b)]
-        bad = fn(nx, ny, nz, (ctypes.c_int * 3)(*per), *[a.ctypes.data_as(ctypes.c_void_p) for a in args],
-                 x.ctypes.data_as(ctypes.c_void_p), first, zero, slab)
+        start = np.full(shape, np.nan) if zero else xin
+        got, bad = _sweep(lib, dtype, shape, per, diag, w, b, start, first, zero)
         assert bad == 0
-        np.testing.assert_allclose(x, ref, rtol=tol, atol=tol * np.abs(ref).max())
+        np.testing.assert_allclose(got, ref, rtol=tol, atol=tol * np.abs(ref).max())
 
 
-def test_queue_plan(lib):
-    """Slabs of 8 planes (all of a thinner grid), chunks of 8192 cells' rows: 256^3 gives 32 slabs
-    of 8 planes x 8 row blocks of 32 rows."""
-    out = (ctypes.c_int * 5)()
-    lib.queue_plan(256, 256, 256, 1, out)
-    assert list(out) == [8, 32, 32, 8, 64]
-    lib.queue_plan(16, 16, 4, 0, out)
-    assert list(out) == [4, 1, 16, 1, 4]
-
-
-@pytest.mark.parametrize("shape,per,zc", [CASES[0], CASES[1], CASES[3], CASES[4]])
-def test_fused_sweep_with_coarse_correction(lib, shape, per, zc):
+@pytest.mark.parametrize("shape,per", [CASES[0], CASES[1], CASES[3], CASES[4]])
+def test_prolongation_is_trilinear(lib, shape, per):
     rng = np.random.default_rng(7)
-    dtype = np.float64
-    diag, *w = _operator(shape, per, rng, dtype)
-    b = rng.standard_normal(shape)
-    x0 = rng.standard_normal(shape)
     cshape = tuple(n // 2 for n in shape)
     xc = rng.standard_normal(cshape)
-    ref = _rbgs_reference(diag, w, b, x0 + _prolong_reference(xc, shape, per), 1)
-    got, bad = _call(lib, dtype, shape, per, diag, w, b, x0, 1, 0, zc, xc=xc)
+    nz, ny, nx = shape
+    out = np.zeros(shape)
+    bad = lib.prolong_host(nx, ny, nz, (ctypes.c_int * 3)(*per), xc.ctypes.data_as(ctypes.c_void_p), cshape[2],
+                           cshape[1], cshape[0], out.ctypes.data_as(ctypes.c_void_p))
     assert bad == 0
-    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
-
-
-def test_chunking_fills_the_resident_ctas(lib):
-    """Work items of 16 planes while they fill the resident CTAs (256^3: 8 x 32 columns, 16 chunks,
-    4096 items), halved down to 4 planes for small levels."""
-    lib.sweep_chunk_planes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong]
-    assert lib.sweep_chunk_planes(256, 256, 256, 912) == 16
-    assert lib.sweep_chunk_planes(64, 64, 64, 912) == 4
-    assert lib.sweep_chunk_planes(16, 16, 2, 912) == 2
+    np.testing.assert_allclose(out, _prolong_reference(xc, shape, per), rtol=1e-14, atol=1e-14)
