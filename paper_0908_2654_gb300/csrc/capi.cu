@@ -162,7 +162,8 @@ struct rt_grid {
     // multigrid
     Hierarchy<float> mgf;
     Hierarchy<double> mgd;
-    float *bf, *xf;           // FP32 level-0 right side / solution (mixed)
+    float *bf, *xf;           // FP32 level-0 right side / solution (mixed), multigrid order
+    double *bs, *xs;          // FP64 level-0 right side / solution in colour-split order
     // reductions
     double *partials, *dots, *scal;
     int* d_err;
@@ -249,12 +250,13 @@ void harvest(rt_grid* g) {
 
 enum HierarchyStatus { HIER_OK = 0, HIER_ODD, HIER_NOMEM };
 
-// lv[0] takes diag0 (freed with the grid) whatever the outcome
+// lv[0] takes diag0 (freed with the grid) whatever the outcome.  Every level but the last is
+// smoothed and gets the colour-split copy of its operator (ds, w6).
 template <class T>
 HierarchyStatus build_hierarchy(rt_grid* g, Hierarchy<T>& H, T* diag0, T* wx0, T* wy0, T* wz0) {
     bool ok = true;
     Dims d = g->dims;
-    Level<T> L;
+    Level<T> L{};
     L.d = d;
     L.diag = diag0;
     L.wx = wx0;
@@ -268,7 +270,7 @@ HierarchyStatus build_hierarchy(rt_grid* g, Hierarchy<T>& H, T* diag0, T* wx0, T
         d.nx /= 2;
         d.ny /= 2;
         d.nz /= 2;
-        Level<T> c;
+        Level<T> c{};
         c.d = d;
         const size_t n = (size_t)d.n();
         c.diag = dalloc<T>(n, ok);
@@ -280,6 +282,16 @@ HierarchyStatus build_hierarchy(rt_grid* g, Hierarchy<T>& H, T* diag0, T* wx0, T
         for (void* p : {(void*)c.diag, (void*)c.wx, (void*)c.wy, (void*)c.wz, (void*)c.x, (void*)c.b}) H.owned.push_back(p);
         if (!ok) return HIER_NOMEM;
         H.lv.push_back(c);
+    }
+    for (size_t l = 0; l + 1 < H.lv.size(); ++l) {
+        Level<T>& s = H.lv[l];
+        const size_t n = (size_t)s.d.n();
+        s.split = 1;
+        s.ds = dalloc<T>(n, ok);
+        s.w6 = dalloc<T>(3 * n, ok);
+        H.owned.push_back(s.ds);
+        H.owned.push_back(s.w6);
+        if (!ok) return HIER_NOMEM;
     }
     return HIER_OK;
 }
@@ -296,6 +308,10 @@ void mg_setup(rt_grid* g, Hierarchy<T>& H) {
     for (size_t l = 1; l < H.lv.size(); ++l) {
         const double fine = (double)H.lv[l - 1].d.n();
         run(g, K_COARSEN, fine * 4.5 * sizeof(T), [&] { launch_coarsen<T>(H.lv[l - 1], H.lv[l], g->stream); });
+    }
+    for (size_t l = 0; l + 1 < H.lv.size(); ++l) {
+        const double n = (double)H.lv[l].d.n();
+        run(g, K_COARSEN, n * 8 * sizeof(T), [&] { launch_split_level<T>(H.lv[l], g->stream); });
     }
 }
 
@@ -346,17 +362,25 @@ void precondition(rt_grid* g, const double* r) {
         // r is scaled by a power of two (from max|r| in dots[1], left there by the residual
         // update) so that the FP32 copy neither overflows nor underflows; z is scaled back
         const double* amax = g->dots + 1;
-        run(g, K_CAST, n * 12, [&] { launch_cast_d2f_scaled(g->n, r, g->bf, amax, s); });
         Level<float>& L0 = g->mgf.lv[0];
+        run(g, K_CAST, n * 12, [&] { launch_to_level<double, float>(g->dims, L0.split, r, g->bf, amax, s); });
         L0.b = g->bf;
         L0.x = g->xf;
         vcycle<float>(g, g->mgf);
-        run(g, K_CAST, n * 12, [&] { launch_cast_f2d_scaled(g->n, g->xf, g->z, amax, s); });
+        run(g, K_CAST, n * 12, [&] { launch_from_level<float, double>(g->dims, L0.split, g->xf, g->z, amax, s); });
     } else {
         Level<double>& L0 = g->mgd.lv[0];
-        L0.b = const_cast<double*>(r);
-        L0.x = g->z;
+        if (L0.split) {
+            run(g, K_CAST, n * 16, [&] { launch_to_level<double, double>(g->dims, 1, r, g->bs, nullptr, s); });
+            L0.b = g->bs;
+            L0.x = g->xs;
+        } else {
+            L0.b = const_cast<double*>(r);
+            L0.x = g->z;
+        }
         vcycle<double>(g, g->mgd);
+        if (L0.split)
+            run(g, K_CAST, n * 16, [&] { launch_from_level<double, double>(g->dims, 1, g->xs, g->z, nullptr, s); });
     }
 }
 
@@ -750,6 +774,8 @@ void rt_destroy_grid(rt_grid* g) {
     cudaFree(g->wzf);
     cudaFree(g->bf);
     cudaFree(g->xf);
+    cudaFree(g->bs);
+    cudaFree(g->xs);
     cudaFree(g->d_err);
     if (g->mgf.lv.size() > 0) cudaFree(g->mgf.lv[0].diag);
     if (g->mgd.lv.size() > 0) cudaFree(g->mgd.lv[0].diag);
@@ -861,6 +887,10 @@ int rt_init_grid(const rt_grid_desc* desc, rt_grid** out) {
                 return RT_EINVAL;
             }
             if (hs == HIER_NOMEM) ok = false;
+            if (ok && g->mgd.lv[0].split) {
+                g->bs = dalloc<double>(n, ok);
+                g->xs = dalloc<double>(n, ok);
+            }
         }
     }
     if (!ok) {

@@ -185,6 +185,9 @@ void launch_add(long long n, const double* a, double* b, cudaStream_t s);   // b
 void launch_cg_scalars(double* scal, const double* dots, int phase, cudaStream_t s);
 
 // ---- multigrid (T = float or double)
+// Every level but the last is smoothed and holds x and b colour-split (rbpass.cuh), with the
+// smoother's copy of its operator in ds / w6; the last level, solved by the single-CTA solver,
+// is in natural order.  diag / wx / wy / wz are the natural-order operator of every level.
 template <class T>
 struct Level {
     Dims d;
@@ -192,20 +195,32 @@ struct Level {
     T* wx;
     T* wy;
     T* wz;
+    T* ds;     // colour-split diagonal (split levels)
+    T* w6;     // six face arrays of the colour-0 cells, n/2 each (split levels)
     T* x;      // current iterate
     T* b;
+    int split; // x and b colour-split
 };
 template <class T>
 void launch_coarsen(const Level<T>& f, const Level<T>& c, cudaStream_t s);
-// one red-black Gauss-Seidel sweep of L.x in place as two colour passes (rbpass.cuh), the first
-// from a zero iterate when zero_guess; returns the launches made
+// ds and w6 of a split level from its natural-order operator
+template <class T>
+void launch_split_level(const Level<T>& L, cudaStream_t s);
+// one red-black Gauss-Seidel sweep of a split level's x in place as two colour passes
+// (rbpass.cuh), the first from a zero iterate when zero_guess; returns the launches made
 template <class T>
 int launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, cudaStream_t s);
-// f.x += trilinear prolongation of c.x
+// f.x += trilinear prolongation of c.x (f split)
 template <class T>
 void launch_prolong_add(const Level<T>& c, const Level<T>& f, cudaStream_t s);
+// c.b = average over the 8 children of f.b - S f.x (f split)
 template <class T>
 void launch_resid_restrict(const Level<T>& f, const Level<T>& c, cudaStream_t s);
+// level-0 vectors: out[level order] = a * 2^-k (k from *amax, or 0 when amax is null) and back
+template <class Tin, class Tout>
+void launch_to_level(const Dims& d, int split, const Tin* a, Tout* out, const double* amax, cudaStream_t s);
+template <class Tin, class Tout>
+void launch_from_level(const Dims& d, int split, const Tin* a, Tout* out, const double* amax, cudaStream_t s);
 template <class T>
 int launch_tail(const Level<T>& L, int ncycles, int nu, cudaStream_t s);
 template <class T>

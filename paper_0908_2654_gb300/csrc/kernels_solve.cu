@@ -6,10 +6,10 @@
 //  * FP64 conjugate-gradient vector kernels (matrix-vector product with fused dot product,
 //    fused x/r update with the residual norm, fused dot pairs) -- HBM-bound streams;
 //  * geometric multigrid, templated on the working precision T (float for the mixed path):
-//      - red-black Gauss-Seidel sweeps, each one pass over HBM on shared-memory plane tiles
-//        (smoother.cuh), the first post-smoothing sweep taking the trilinear cell-centred
-//        prolongation of the coarse correction on the fly;
-//      - fused residual + restriction (average of the 8 children);
+//      - red-black Gauss-Seidel sweeps as two in-place colour passes over a colour-split
+//        storage of each smoothed level (rbpass.cuh);
+//      - fused residual + restriction (average of the 8 children) and the trilinear
+//        cell-centred prolongation of the coarse correction added to the fine iterate;
 //      - coarse operators by averaging: sigma_c = geometric mean of the children's
 //        sigma = diag - sum w, coarse face coupling = sum of the 4 fine face couplings / 16
 //        (what re-discretising the diffusion term on the doubled cell gives for constant
@@ -206,17 +206,29 @@ __device__ __forceinline__ double pow2_scale(double amax, bool inverse) {
     if (amax > 0.0 && isfinite(amax)) frexp(amax, &e);   // amax < 2^e
     return ldexp(1.0, inverse ? e : -e);
 }
-__global__ void k_cast_d2f_scaled(long long n, const double* __restrict__ a, float* __restrict__ b,
-                                  const double* __restrict__ amax) {
-    const double sc = pow2_scale(*amax, false);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        b[i] = (float)(a[i] * sc);
+// level-0 vectors in the multigrid's storage order (colour-split when `split`): thread per
+// natural cell, scaled by 2^-e (2^e >= *amax) on the way in and 2^e on the way out
+template <class Tin, class Tout>
+__global__ void k_to_level(Dims d, int split, const Tin* __restrict__ a, Tout* __restrict__ out,
+                           const double* __restrict__ amax) {
+    const double sc = amax ? pow2_scale(*amax, false) : 1.0;
+    const long long n = d.n();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        cell_coords(i, d.nx, d.ny, x, y, z);
+        out[rbp::level_index(split, d.nx, d.ny, d.nz, x, y, z)] = (Tout)((double)a[i] * sc);
+    }
 }
-__global__ void k_cast_f2d_scaled(long long n, const float* __restrict__ a, double* __restrict__ b,
-                                  const double* __restrict__ amax) {
-    const double sc = pow2_scale(*amax, true);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        b[i] = (double)a[i] * sc;
+template <class Tin, class Tout>
+__global__ void k_from_level(Dims d, int split, const Tin* __restrict__ a, Tout* __restrict__ out,
+                             const double* __restrict__ amax) {
+    const double sc = amax ? pow2_scale(*amax, true) : 1.0;
+    const long long n = d.n();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        cell_coords(i, d.nx, d.ny, x, y, z);
+        out[i] = (Tout)((double)a[rbp::level_index(split, d.nx, d.ny, d.nz, x, y, z)] * sc);
+    }
 }
 __global__ void k_cast_f2d(long long n, const float* __restrict__ a, double* __restrict__ b) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -250,26 +262,59 @@ __global__ void k_cg_scalars(double* scal, const double* dots, int phase) {
 
 // ------------------------------------------------------------------- multigrid kernels
 
-// one colour pass of a red-black sweep over planes [z0, z0 + gridDim.z) in place (rbpass.cuh)
-template <class T>
+// one colour pass (colour C) of a red-black sweep of a colour-split level in place (rbpass.cuh)
+template <int C, class T>
 __global__ void __launch_bounds__(rbp::kPairs) k_rbgs_pass(rbp::Pass<T> A) {
     int x, y, z;
     if (!rbp::pair_cell(A, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, x, y, z)) return;
-    A.x[(long long)z * A.nx * A.ny + (long long)y * A.nx + x] = rbp::cell_value(A, x, y, z);
+    const long long half = (long long)(A.nx >> 1) * A.ny * A.nz;
+    const long long m = ((long long)z * A.ny + y) * (A.nx >> 1) + (x >> 1);
+    A.x[C * half + m] = rbp::cell_value<C>(A, x, y, z);
 }
 
-// x += P xc: trilinear cell-centred prolongation of the coarse correction
+// the smoother's copy of a level's operator (colour-split diagonal, colour-0 face arrays)
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_split_level(Level<T> L) {
+    const long long half = L.d.n() / 2;
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < half; m += (long long)gridDim.x * blockDim.x)
+        rbp::split_pair(L.d.nx, L.d.ny, L.d.nz, L.d.per, L.diag, L.wx, L.wy, L.wz, m, L.ds, L.w6);
+}
+
+// x += P xc: trilinear cell-centred prolongation of the coarse correction; thread per fine pair
+// (both cells share the coarse cell and one store into each colour half)
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_prolong_add(Level<T> c, Level<T> f) {
     const Dims fd = f.d;
-    const int nxy = fd.nx * fd.ny;
-    const long long n = fd.n();
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int z = (int)(i / nxy);
-        const int r = (int)(i - (long long)z * nxy);
-        const int y = r / fd.nx, x = r - y * fd.nx;
-        f.x[i] += rbp::prolong_at(c.x, c.d.nx, c.d.ny, c.d.nz, c.d.per, x, y, z);
+    const int hx = fd.nx >> 1;
+    const long long half = fd.n() / 2;
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < half; m += (long long)gridDim.x * blockDim.x) {
+        const long long r = m / hx;
+        const int px = (int)(m - r * hx);
+        const int z = (int)(r / fd.ny), y = (int)(r - (long long)z * fd.ny);
+#pragma unroll
+        for (int o = 0; o < 2; ++o) {
+            const int x = 2 * px + o;
+            f.x[(long long)((x + y + z) & 1) * half + m] +=
+                rbp::prolong_at(c.x, c.split, c.d.nx, c.d.ny, c.d.nz, c.d.per, x, y, z);
+        }
     }
+}
+
+// b - S x at fine cell (x, y, z) of a colour-split level (operator in natural order)
+template <class T>
+__device__ __forceinline__ T split_residual(const Level<T>& f, int x, int y, int z) {
+    const Dims& d = f.d;
+    const long long i = ((long long)z * d.ny + y) * d.nx + x;
+    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
+    auto X = [&](int a, int b, int e) { return f.x[rbp::level_index(1, d.nx, d.ny, d.nz, a, b, e)]; };
+    const T wxm = (!d.per[0] && x == 0) ? T(0) : f.wx[x > 0 ? i - 1 : i - 1 + d.nx];
+    const T wym = (!d.per[1] && y == 0) ? T(0) : f.wy[y > 0 ? i - sy : i - sy + sz];
+    const T wzm = (!d.per[2] && z == 0) ? T(0) : f.wz[z > 0 ? i - sz : i - sz + sz * d.nz];
+    const T off = f.wx[i] * X(up(x, d.nx, d.per[0]), y, z) + wxm * X(dn(x, d.nx, d.per[0]), y, z) +
+                  f.wy[i] * X(x, up(y, d.ny, d.per[1]), z) + wym * X(x, dn(y, d.ny, d.per[1]), z) +
+                  f.wz[i] * X(x, y, up(z, d.nz, d.per[2])) + wzm * X(x, y, dn(z, d.nz, d.per[2]));
+    const long long s = rbp::level_index(1, d.nx, d.ny, d.nz, x, y, z);
+    return f.b[s] - (f.diag[i] * f.x[s] - off);
 }
 
 template <class T>
@@ -285,12 +330,8 @@ __global__ void __launch_bounds__(kBlock) k_resid_restrict(Level<T> f, Level<T> 
 #pragma unroll
             for (int j = 0; j < 2; ++j)
 #pragma unroll
-                for (int l = 0; l < 2; ++l) {
-                    const int x = 2 * X + l, y = 2 * Y + j, z = 2 * Z + k;
-                    const long long i = ((long long)z * f.d.ny + y) * f.d.nx + x;
-                    sum += f.b[i] - apply_S<T, T>(i, x, y, z, f.d, f.diag, f.wx, f.wy, f.wz, f.x);
-                }
-        c.b[I] = sum * T(0.125);
+                for (int l = 0; l < 2; ++l) sum += split_residual(f, 2 * X + l, 2 * Y + j, 2 * Z + k);
+        c.b[rbp::level_index(c.split, cd.nx, cd.ny, cd.nz, X, Y, Z)] = sum * T(0.125);
     }
 }
 
@@ -632,12 +673,19 @@ void launch_cast_d2f(long long n, const double* a, float* b, cudaStream_t s) {
 void launch_cast_f2d(long long n, const float* a, double* b, cudaStream_t s) {
     k_cast_f2d<<<grid_for(n), kBlock, 0, s>>>(n, a, b);
 }
-void launch_cast_d2f_scaled(long long n, const double* a, float* b, const double* amax, cudaStream_t s) {
-    k_cast_d2f_scaled<<<grid_for(n), kBlock, 0, s>>>(n, a, b, amax);
+template <class Tin, class Tout>
+void launch_to_level(const Dims& d, int split, const Tin* a, Tout* out, const double* amax, cudaStream_t s) {
+    k_to_level<Tin, Tout><<<grid_for(d.n()), kBlock, 0, s>>>(d, split, a, out, amax);
 }
-void launch_cast_f2d_scaled(long long n, const float* a, double* b, const double* amax, cudaStream_t s) {
-    k_cast_f2d_scaled<<<grid_for(n), kBlock, 0, s>>>(n, a, b, amax);
+template <class Tin, class Tout>
+void launch_from_level(const Dims& d, int split, const Tin* a, Tout* out, const double* amax, cudaStream_t s) {
+    k_from_level<Tin, Tout><<<grid_for(d.n()), kBlock, 0, s>>>(d, split, a, out, amax);
 }
+template void launch_to_level<double, float>(const Dims&, int, const double*, float*, const double*, cudaStream_t);
+template void launch_to_level<double, double>(const Dims&, int, const double*, double*, const double*, cudaStream_t);
+template void launch_from_level<float, double>(const Dims&, int, const float*, double*, const double*, cudaStream_t);
+template void launch_from_level<double, double>(const Dims&, int, const double*, double*, const double*,
+                                                cudaStream_t);
 void launch_copy(long long n, const double* a, double* b, cudaStream_t s) { k_copy<<<grid_for(n), kBlock, 0, s>>>(n, a, b); }
 void launch_add(long long n, const double* a, double* b, cudaStream_t s) { k_add<<<grid_for(n), kBlock, 0, s>>>(n, a, b); }
 void launch_cg_scalars(double* scal, const double* dots, int phase, cudaStream_t s) {
@@ -660,6 +708,11 @@ void launch_coarsen(const Level<T>& f, const Level<T>& c, cudaStream_t s) {
 }
 
 template <class T>
+void launch_split_level(const Level<T>& L, cudaStream_t s) {
+    k_split_level<T><<<grid_for(L.d.n() / 2), kBlock, 0, s>>>(L);
+}
+
+template <class T>
 int launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, cudaStream_t s) {
     const Dims& d = L.d;
     for (int pass = 0; pass < 2; ++pass) {
@@ -668,27 +721,27 @@ int launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, cudaStrea
         A.ny = d.ny;
         A.nz = d.nz;
         for (int k = 0; k < 3; ++k) A.per[k] = d.per[k];
-        A.diag = L.diag;
-        A.wx = L.wx;
-        A.wy = L.wy;
-        A.wz = L.wz;
+        A.ds = L.ds;
+        A.w6 = L.w6;
         A.b = L.b;
         A.x = L.x;
         A.colour = pass == 0 ? first : 1 - first;
         A.zero = pass == 0 && zero_guess;
-        A.z0 = 0;
-        A.planes = d.nz;
         A.rev = pass;   // the second pass starts on the planes the first read last
         int gx, gy, gz;
         rbp::pass_grid(d.nx, d.ny, d.nz, gx, gy, gz, A.rows);
-        k_rbgs_pass<T><<<dim3(gx, gy, gz), rbp::kPairs, 0, s>>>(A);
+        const dim3 grid(gx, gy, gz);
+        if (A.colour == 0)
+            k_rbgs_pass<0, T><<<grid, rbp::kPairs, 0, s>>>(A);
+        else
+            k_rbgs_pass<1, T><<<grid, rbp::kPairs, 0, s>>>(A);
     }
     return 2;
 }
 
 template <class T>
 void launch_prolong_add(const Level<T>& c, const Level<T>& f, cudaStream_t s) {
-    k_prolong_add<T><<<grid_for(f.d.n()), kBlock, 0, s>>>(c, f);
+    k_prolong_add<T><<<grid_for(f.d.n() / 2), kBlock, 0, s>>>(c, f);
 }
 
 template <class T>
@@ -712,10 +765,13 @@ int launch_tail(const Level<T>& L, int ncycles, int nu, cudaStream_t s) {
     TailPlan p;
     make_plan(L.d, p);
     const size_t bytes = tail_smem_bytes<T>(L.d);
-    static bool configured = false;
-    if (!configured) {
+    // the attribute is per device: set it on the first launch on each
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !configured[dev]) {
         cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        configured = true;
+        if (dev >= 0 && dev < 64) configured[dev] = true;
     }
     k_tail<T><<<1, kTailThreads, bytes, s>>>(L, ncycles, nu, p);
     return 1;
@@ -723,6 +779,8 @@ int launch_tail(const Level<T>& L, int ncycles, int nu, cudaStream_t s) {
 
 template void launch_coarsen<float>(const Level<float>&, const Level<float>&, cudaStream_t);
 template void launch_coarsen<double>(const Level<double>&, const Level<double>&, cudaStream_t);
+template void launch_split_level<float>(const Level<float>&, cudaStream_t);
+template void launch_split_level<double>(const Level<double>&, cudaStream_t);
 template int launch_rbgs_inplace<float>(const Level<float>&, int, bool, cudaStream_t);
 template int launch_rbgs_inplace<double>(const Level<double>&, int, bool, cudaStream_t);
 template void launch_prolong_add<float>(const Level<float>&, const Level<float>&, cudaStream_t);

@@ -1,16 +1,23 @@
-// Red-black Gauss-Seidel sweeps of a multigrid level as two in-place colour passes, and the
-// trilinear prolongation of a coarse correction.
+// Red-black Gauss-Seidel sweeps of a multigrid level as two in-place colour passes over a
+// colour-split storage of the level, and the trilinear prolongation of a coarse correction.
 //
-// The level's operator is (S x)_i = diag_i x_i - sum_faces w_f x_nb (w on each cell's +x/+y/+z
-// face, zero on boundary faces).  A sweep sets every cell of the first colour (parity of x + y + z
-// equal to `first`) from its neighbours, which all have the other colour, then every cell of the
-// other colour from the new first-colour values, both in place.
+// The level's operator is (S x)_i = diag_i x_i - sum_faces w_f x_nb.  A sweep sets every cell of
+// the first colour (parity of x + y + z equal to `first`) from its neighbours, which all have the
+// other colour, then every cell of the other colour from the new first-colour values.
 //
-// A pass is one kernel launch with one thread per pair of x-neighbours (one cell of each colour),
-// a block per row segment and plane, and no loop, barrier or division: all SM resources go to
-// keeping loads in flight.  The second pass takes the planes in reverse order, so that it starts
-// on the planes the first pass read last (still in L2), and the next sweep's first pass starts on
-// the planes this second pass read last.
+// Storage (levels with even nx, ny, nz): each x-pair of cells (2p, 2p + 1) holds one cell of each
+// colour, so pair m = (z ny + y) nx/2 + p indexes both colour halves: the cell of colour c of
+// pair m sits at c * n/2 + m in x, b and the diagonal.  Every face joins a colour-0 cell to a
+// colour-1 cell, so the 3n face couplings are stored once, as the six faces of the colour-0 cells
+// (face arrays of n/2 each, in the order -x, +x, -y, +y, -z, +z).  A colour pass then streams
+// contiguous arrays only: its own half of b and the diagonal, all six face arrays, the other
+// colour's half of x (neighbours at pair offsets 0, +-1, +-nx/2, +-nx ny/2) and its own half of x
+// written: 5 words per cell of the level per pass.  In natural order a pass over one colour moves
+// every sector of b, diag, x, wx, wy, wz (half of each used) and rewrites half of x: about 7.
+//
+// A pass is one kernel launch with one thread per pair, a block per row segment and plane, and no
+// loop, barrier or division.  The second pass takes the planes in reverse order, so that it starts
+// on the planes the first pass read last (still in L2).
 //
 // The functions are host/device so that a host build can run the passes and compare them with a
 // plain sweep (tests/host/smoother_host.cu).
@@ -27,21 +34,26 @@
 namespace rbp {
 
 constexpr int kPairs = 128;   // threads (pairs) per block
+enum Face { FXM = 0, FXP = 1, FYM = 2, FYP = 3, FZM = 4, FZP = 5 };
+
+// storage index of cell (x, y, z) in a colour-split level (even nx) or in natural order
+RT_HD long long level_index(int split, int nx, int ny, int nz, int x, int y, int z) {
+    const long long i = ((long long)z * ny + y) * nx + x;
+    if (!split) return i;
+    const long long half = (long long)nx * ny * nz / 2;
+    return (long long)((x + y + z) & 1) * half + (i >> 1);
+}
 
 template <class T>
 struct Pass {
     int nx, ny, nz;
     int per[3];
-    const T* diag;
-    const T* wx;
-    const T* wy;
-    const T* wz;
-    const T* b;
-    T* x;
+    const T* ds;    // diagonal, colour-split
+    const T* w6;    // six face arrays of the colour-0 cells
+    const T* b;     // colour-split
+    T* x;           // colour-split, updated in place
     int colour;     // parity of the cells this pass sets
     int zero;       // the old iterate is zero (first pass of a sweep from zero)
-    int z0;         // first plane of the pass
-    int planes;     // planes of the pass
     int rev;        // blocks take the planes from the last to the first
     int rows;       // rows per block: kPairs / pairs per row (at least 1)
 };
@@ -50,7 +62,7 @@ struct Pass {
 // it has no cell
 template <class T>
 RT_HD bool pair_cell(const Pass<T>& A, int bx, int by, int bz, int t, int& x, int& y, int& z) {
-    const int hp = (A.nx + 1) >> 1;
+    const int hp = A.nx >> 1;
     int px, ry;
     if (A.rows == 1) {
         px = bx * kPairs + t;
@@ -60,40 +72,52 @@ RT_HD bool pair_cell(const Pass<T>& A, int bx, int by, int bz, int t, int& x, in
         px = t - ry * hp;
     }
     y = by * A.rows + ry;
-    z = A.z0 + (A.rev ? A.planes - 1 - bz : bz);
+    z = A.rev ? A.nz - 1 - bz : bz;
     if (px >= hp || y >= A.ny || ry >= A.rows) return false;
     x = 2 * px + ((y + z + A.colour) & 1);   // the pair's cell of this colour
-    return x < A.nx;
+    return true;
 }
 
-// new value of cell (x, y, z) from its neighbours
-template <class T>
+// neighbour pairs of cell (x, y, z) (pair m) in face order; -1 across a non-periodic boundary.
+// The neighbour across face f has the other colour; for a colour-1 cell the coupling of face f
+// is the opposite face (f ^ 1) of that colour-0 neighbour.
+RT_HD void neighbour_pairs(int nx, int ny, int nz, const int* per, int x, int y, int z, long long m, long long* q) {
+    const long long hx = nx >> 1, hxy = hx * ny, half = hxy * nz;
+    const int odd = x & 1;
+    q[FXM] = odd ? m : (x > 0 ? m - 1 : (per[0] ? m - 1 + hx : -1));
+    q[FXP] = !odd ? m : (x + 1 < nx ? m + 1 : (per[0] ? m + 1 - hx : -1));
+    q[FYM] = y > 0 ? m - hx : (per[1] ? m - hx + hxy : -1);
+    q[FYP] = y + 1 < ny ? m + hx : (per[1] ? m + hx - hxy : -1);
+    q[FZM] = z > 0 ? m - hxy : (per[2] ? m - hxy + half : -1);
+    q[FZP] = z + 1 < nz ? m + hxy : (per[2] ? m + hxy - half : -1);
+}
+
+// new value of cell (x, y, z) of colour C from its neighbours
+template <int C, class T>
 RT_HD T cell_value(const Pass<T>& A, int x, int y, int z) {
-    const long long sy = A.nx, sz = (long long)A.nx * A.ny;
-    const long long i = (long long)z * sz + (long long)y * sy + x;
-    RT_SWEEP_CHECK(i >= 0 && i < sz * A.nz);
-    T num = A.b[i];
+    const long long hx = A.nx >> 1, half = hx * A.ny * A.nz;
+    const long long m = ((long long)z * A.ny + y) * hx + (x >> 1);
+    RT_SWEEP_CHECK(m >= 0 && m < half);
+    const long long own = C * half + m;
+    T num = A.b[own];
     if (!A.zero) {
-        if (x + 1 < A.nx) num += A.wx[i] * A.x[i + 1];
-        else if (A.per[0]) num += A.wx[i] * A.x[i + 1 - A.nx];
-        if (x > 0) num += A.wx[i - 1] * A.x[i - 1];
-        else if (A.per[0]) num += A.wx[i - 1 + A.nx] * A.x[i - 1 + A.nx];
-        if (y + 1 < A.ny) num += A.wy[i] * A.x[i + sy];
-        else if (A.per[1]) num += A.wy[i] * A.x[i + sy - sz];
-        if (y > 0) num += A.wy[i - sy] * A.x[i - sy];
-        else if (A.per[1]) num += A.wy[i - sy + sz] * A.x[i - sy + sz];
-        const long long sv = sz * A.nz;
-        if (z + 1 < A.nz) num += A.wz[i] * A.x[i + sz];
-        else if (A.per[2]) num += A.wz[i] * A.x[i + sz - sv];
-        if (z > 0) num += A.wz[i - sz] * A.x[i - sz];
-        else if (A.per[2]) num += A.wz[i - sz + sv] * A.x[i - sz + sv];
+        const T* xo = A.x + (1 - C) * half;
+        long long q[6];
+        neighbour_pairs(A.nx, A.ny, A.nz, A.per, x, y, z, m, q);
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            if (q[f] < 0) continue;
+            RT_SWEEP_CHECK(q[f] < half);
+            const T w = C == 0 ? A.w6[f * half + m] : A.w6[(f ^ 1) * half + q[f]];
+            num += w * xo[q[f]];
+        }
     }
-    return num / A.diag[i];
+    return num / A.ds[own];
 }
 
-// launch geometry of a pass over `planes` planes: (blocks per row, row blocks, planes)
-inline void pass_grid(int nx, int ny, int planes, int& gx, int& gy, int& gz, int& rows) {
-    const int hp = (nx + 1) / 2;
+// launch geometry of a pass: (blocks per row, row blocks, planes)
+inline void pass_grid(int nx, int ny, int nz, int& gx, int& gy, int& gz, int& rows) {
+    const int hp = nx / 2;
     if (hp >= kPairs) {
         rows = 1;
         gx = (hp + kPairs - 1) / kPairs;
@@ -102,14 +126,39 @@ inline void pass_grid(int nx, int ny, int planes, int& gx, int& gy, int& gz, int
         gx = 1;
     }
     gy = (ny + rows - 1) / rows;
-    gz = planes;
+    gz = nz;
+}
+
+// colour-split diagonal and colour-0 face arrays of pair m from the natural diagonal and the
+// couplings on each cell's +x/+y/+z face (zero on a non-periodic boundary face)
+template <class T>
+RT_HD void split_pair(int nx, int ny, int nz, const int* per, const T* diag, const T* wx, const T* wy, const T* wz,
+                      long long m, T* ds, T* w6) {
+    const long long hx = nx >> 1, half = hx * ny * nz;
+    const long long r = m / hx;
+    const int px = (int)(m - r * hx), y = (int)(r % ny), z = (int)(r / ny);
+    const long long sy = nx, sz = (long long)nx * ny, sv = sz * nz;
+    for (int o = 0; o < 2; ++o) {
+        const int x = 2 * px + o;
+        const long long i = 2 * m + o;
+        RT_SWEEP_CHECK(i >= 0 && i < sv);
+        const int c = (x + y + z) & 1;
+        ds[c * half + m] = diag[i];
+        if (c) continue;
+        w6[FXM * half + m] = x > 0 ? wx[i - 1] : (per[0] ? wx[i - 1 + nx] : T(0));
+        w6[FXP * half + m] = x + 1 < nx || per[0] ? wx[i] : T(0);
+        w6[FYM * half + m] = y > 0 ? wy[i - sy] : (per[1] ? wy[i - sy + sz] : T(0));
+        w6[FYP * half + m] = y + 1 < ny || per[1] ? wy[i] : T(0);
+        w6[FZM * half + m] = z > 0 ? wz[i - sz] : (per[2] ? wz[i - sz + sv] : T(0));
+        w6[FZP * half + m] = z + 1 < nz || per[2] ? wz[i] : T(0);
+    }
 }
 
 // coarse-cell value of the trilinear cell-centred prolongation at fine cell (x, y, z): weights
 // 3/4 and 1/4 along each axis from the coarse cell holding the fine cell and its neighbour on the
-// fine cell's side (the cell itself at a non-periodic edge)
+// fine cell's side (the cell itself at a non-periodic edge); xc colour-split when csplit
 template <class T>
-RT_HD T prolong_at(const T* xc, int cnx, int cny, int cnz, const int* per, int x, int y, int z) {
+RT_HD T prolong_at(const T* xc, int csplit, int cnx, int cny, int cnz, const int* per, int x, int y, int z) {
     const int X = x >> 1, Y = y >> 1, Z = z >> 1;
     auto other = [](int C, int odd, int n, int p) {
         const int c = odd ? C + 1 : C - 1;
@@ -119,10 +168,9 @@ RT_HD T prolong_at(const T* xc, int cnx, int cny, int cnz, const int* per, int x
     const int X2 = other(X, x & 1, cnx, per[0]);
     const int Y2 = other(Y, y & 1, cny, per[1]);
     const int Z2 = other(Z, z & 1, cnz, per[2]);
-    const long long sy = cnx, sz = (long long)cnx * cny;
     auto C = [&](int a, int b, int e) {
-        const long long j = (long long)e * sz + (long long)b * sy + a;
-        RT_SWEEP_CHECK(j >= 0 && j < sz * cnz);
+        const long long j = level_index(csplit, cnx, cny, cnz, a, b, e);
+        RT_SWEEP_CHECK(j >= 0 && j < (long long)cnx * cny * cnz);
         return xc[j];
     };
     const T w1 = T(0.75), w2 = T(0.25);

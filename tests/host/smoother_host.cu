@@ -1,6 +1,7 @@
-// Host build of the multigrid level kernels' cell functions (rbpass.cuh): the two in-place
-// colour passes of a red-black sweep, every block and thread of each launch in turn, and the
-// trilinear prolongation, with a check on every global index they form.
+// Host build of the multigrid level functions (rbpass.cuh): the colour-split storage of a level
+// (its operator and vectors), the two in-place colour passes of a red-black sweep on it, every
+// block and thread of each launch in turn, and the trilinear prolongation from a natural or
+// colour-split coarse vector, with a check on every index they form.
 #include <vector>
 
 static long long g_bad_index = 0;
@@ -19,26 +20,46 @@ template <class T>
 static long long run_sweep(int nx, int ny, int nz, const int* per, const T* diag, const T* wx, const T* wy,
                            const T* wz, const T* b, T* x, int first, int zero) {
     g_bad_index = 0;
+    const long long n = (long long)nx * ny * nz, half = n / 2;
+    // the level in colour-split storage
+    std::vector<T> ds(n, T(-1)), w6(3 * n, T(-1)), bs(n), xs(n);
+    for (long long m = 0; m < half; ++m) rbp::split_pair(nx, ny, nz, per, diag, wx, wy, wz, m, ds.data(), w6.data());
+    std::vector<int> seen(n, 0);
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int xx = 0; xx < nx; ++xx) {
+                const long long i = ((long long)z * ny + y) * nx + xx;
+                const long long s = rbp::level_index(1, nx, ny, nz, xx, y, z);
+                if (s < 0 || s >= n) {
+                    ++g_bad_index;
+                    continue;
+                }
+                ++seen[s];
+                bs[s] = b[i];
+                xs[s] = x[i];
+            }
+    for (long long s = 0; s < n; ++s)
+        if (seen[s] != 1) ++g_bad_index;   // level_index is a bijection
+    for (long long k = 0; k < n; ++k)
+        if (ds[k] == T(-1)) ++g_bad_index;   // every diagonal entry written
+    for (long long k = 0; k < 3 * n; ++k)
+        if (w6[k] == T(-1)) ++g_bad_index;   // every face entry written
     for (int pass = 0; pass < 2; ++pass) {
         rbp::Pass<T> A;
         A.nx = nx;
         A.ny = ny;
         A.nz = nz;
         for (int q = 0; q < 3; ++q) A.per[q] = per[q];
-        A.diag = diag;
-        A.wx = wx;
-        A.wy = wy;
-        A.wz = wz;
-        A.b = b;
-        A.x = x;
+        A.ds = ds.data();
+        A.w6 = w6.data();
+        A.b = bs.data();
+        A.x = xs.data();
         A.colour = pass == 0 ? first : 1 - first;
         A.zero = pass == 0 && zero;
-        A.z0 = 0;
-        A.planes = nz;
         A.rev = pass;
         int gx, gy, gz;
         rbp::pass_grid(nx, ny, nz, gx, gy, gz, A.rows);
-        std::vector<int> hits((size_t)nx * ny * nz, 0);
+        std::vector<int> hits(n, 0);
         // a pass never reads the cells it sets, so the order of its threads does not matter
         for (int bz = 0; bz < gz; ++bz)
             for (int by = 0; by < gy; ++by)
@@ -46,22 +67,26 @@ static long long run_sweep(int nx, int ny, int nz, const int* per, const T* diag
                     for (int t = 0; t < rbp::kPairs; ++t) {
                         int cx, cy, cz;
                         if (!rbp::pair_cell(A, bx, by, bz, t, cx, cy, cz)) continue;
-                        const long long i = ((long long)cz * ny + cy) * nx + cx;
-                        if (!(i >= 0 && i < (long long)nx * ny * nz)) {
+                        if (cx < 0 || cx >= nx || cy < 0 || cy >= ny || cz < 0 || cz >= nz) {
                             ++g_bad_index;
                             continue;
                         }
-                        ++hits[i];
-                        x[i] = rbp::cell_value(A, cx, cy, cz);
+                        const long long s = rbp::level_index(1, nx, ny, nz, cx, cy, cz);
+                        ++hits[((long long)cz * ny + cy) * nx + cx];
+                        xs[s] = A.colour ? rbp::cell_value<1>(A, cx, cy, cz) : rbp::cell_value<0>(A, cx, cy, cz);
                     }
         // every cell of the pass's colour set exactly once, no other cell touched
         for (int z = 0; z < nz; ++z)
             for (int y = 0; y < ny; ++y)
                 for (int xx = 0; xx < nx; ++xx) {
                     const int want = ((xx + y + z) & 1) == A.colour ? 1 : 0;
-                    if (hits[((size_t)z * ny + y) * nx + xx] != want) ++g_bad_index;
+                    if (hits[((long long)z * ny + y) * nx + xx] != want) ++g_bad_index;
                 }
     }
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int xx = 0; xx < nx; ++xx)
+                x[((long long)z * ny + y) * nx + xx] = xs[rbp::level_index(1, nx, ny, nz, xx, y, z)];
     return g_bad_index;
 }
 
@@ -74,14 +99,21 @@ long long sweep_host_f32(int nx, int ny, int nz, const int* per, const float* di
                          const float* wy, const float* wz, const float* b, float* x, int first, int zero) {
     return run_sweep<float>(nx, ny, nz, per, diag, wx, wy, wz, b, x, first, zero);
 }
-// out[z][y][x] = trilinear prolongation of the coarse vector xc (cnx x cny x cnz) at every fine cell
+// out[z][y][x] = trilinear prolongation at every fine cell of the coarse vector xc (cnx x cny x
+// cnz, natural order), read from a colour-split copy when csplit
 long long prolong_host(int nx, int ny, int nz, const int* per, const double* xc, int cnx, int cny, int cnz,
-                       double* out) {
+                       int csplit, double* out) {
     g_bad_index = 0;
+    const long long nc = (long long)cnx * cny * cnz;
+    std::vector<double> c(nc);
+    for (int Z = 0; Z < cnz; ++Z)
+        for (int Y = 0; Y < cny; ++Y)
+            for (int X = 0; X < cnx; ++X)
+                c[rbp::level_index(csplit, cnx, cny, cnz, X, Y, Z)] = xc[((long long)Z * cny + Y) * cnx + X];
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x)
-                out[((long long)z * ny + y) * nx + x] = rbp::prolong_at(xc, cnx, cny, cnz, per, x, y, z);
+                out[((long long)z * ny + y) * nx + x] = rbp::prolong_at(c.data(), csplit, cnx, cny, cnz, per, x, y, z);
     return g_bad_index;
 }
 }

@@ -1,10 +1,11 @@
 """The red-black Gauss-Seidel sweep of the multigrid levels (rbpass.cuh), compiled for the host
-and run launch by launch, block by block, against a plain red-black Gauss-Seidel sweep written
-from its definition: update every cell of the first colour from its neighbours' old values,
-x_i = (b_i + sum_faces w_f x_nb) / diag_i, then every cell of the other colour from the new
-values.  Also: the zero start, each pass setting exactly the cells of its colour, every global
-index in range, rows shorter and longer than a block, periodic and reflecting axes, odd
-non-periodic dimensions; and the trilinear cell-centred prolongation of a coarse vector."""
+and run launch by launch, block by block, on the colour-split storage of a level against a plain
+red-black Gauss-Seidel sweep in natural order written from its definition: update every cell of
+the first colour from its neighbours' old values, x_i = (b_i + sum_faces w_f x_nb) / diag_i, then
+every cell of the other colour from the new values.  Also: the colour-split index is a bijection,
+the split operator fills every entry, the zero start, each pass setting exactly the cells of its
+colour, every index in range, rows shorter and longer than a block, periodic and reflecting axes;
+and the trilinear cell-centred prolongation of a natural or colour-split coarse vector."""
 import ctypes
 import os
 import shutil
@@ -99,11 +100,12 @@ def _sweep(lib, dtype, shape, per, diag, w, b, xin, first, zero):
     return x, bad
 
 
+# (nz, ny, nx), periodic (x, y, z): split levels have even dimensions
 CASES = [((20, 32, 64), (True, True, True)), ((24, 40, 40), (False, False, False)),
          ((4, 6, 8), (False, True, False)), ((10, 18, 36), (True, False, True)),
          ((12, 20, 34), (False, False, True)), ((8, 8, 8), (True, True, True)),
-         ((6, 4, 300), (True, False, False)), ((37, 8, 10), (False, True, False)),
-         ((24, 6, 8), (True, True, False))]
+         ((6, 4, 300), (True, False, False)), ((2, 8, 2), (False, True, False)),
+         ((24, 6, 8), (True, True, False)), ((2, 2, 258), (True, True, True))]
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
@@ -122,14 +124,15 @@ def test_sweep_equals_red_black_gauss_seidel(lib, shape, per, dtype):
         np.testing.assert_allclose(got, ref, rtol=tol, atol=tol * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("shape,per", [CASES[0], CASES[1], CASES[3], CASES[4]])
-def test_prolongation_is_trilinear(lib, shape, per):
+@pytest.mark.parametrize("csplit", [0, 1])
+@pytest.mark.parametrize("shape,per", [CASES[0], CASES[1], CASES[3], ((40, 24, 48), (False, False, True))])
+def test_prolongation_is_trilinear(lib, shape, per, csplit):
     rng = np.random.default_rng(7)
     cshape = tuple(n // 2 for n in shape)
     xc = rng.standard_normal(cshape)
     nz, ny, nx = shape
     out = np.zeros(shape)
     bad = lib.prolong_host(nx, ny, nz, (ctypes.c_int * 3)(*per), xc.ctypes.data_as(ctypes.c_void_p), cshape[2],
-                           cshape[1], cshape[0], out.ctypes.data_as(ctypes.c_void_p))
+                           cshape[1], cshape[0], csplit, out.ctypes.data_as(ctypes.c_void_p))
     assert bad == 0
     np.testing.assert_allclose(out, _prolong_reference(xc, shape, per), rtol=1e-14, atol=1e-14)
