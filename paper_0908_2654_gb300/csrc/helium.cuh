@@ -97,6 +97,21 @@ RT_HD HeRates<Dual<K>> he_rates(const PhysParams& P, const Dual<K>& temp, bool c
     return o;
 }
 
+// The rates as (value, d/dT) pairs, carried onto the unknowns' lanes only where a rate is used:
+// nine rates held on all lanes at once would not fit the registers of the five-lane Jacobian.
+RT_HD HeRates<double> he_rates_lazy(const PhysParams& P, double temp, bool cool) {
+    return he_rates_direct(P, temp, cool);
+}
+template <int K>
+RT_HD HeRates<Dual<1>> he_rates_lazy(const PhysParams& P, const Dual<K>& temp, bool cool) {
+    return he_rates_direct(P, dvar<1>(temp.v, 0), cool);
+}
+RT_HD double on_lanes(double, double r) { return r; }
+template <int K>
+RT_HD Dual<K> on_lanes(const Dual<K>& temp, const Dual<1>& r) {
+    return dchain(temp, r.v, r.d[0]);
+}
+
 // n(dt) for n' = A (nH - n)(nH + neHe - n) - G n, n(0) = y0
 template <class T>
 RT_HD T riccati_ne(double y0, double nH, const T& neHe, const T& A, const T& G, double dt) {
@@ -179,12 +194,13 @@ RT_HD void local_solutions_he(const PhysParams& P, const CellHe& c, const T& ec,
         if (value(temp) < RT_T_FLOOR) temp = temp * 0.0 + RT_T_FLOOR;
     }
     const bool cool = !P.isothermal && P.cooling;
-    const HeRates<T> r = he_rates(P, temp, cool);
+    const auto r = he_rates_lazy(P, temp, cool);
     const double rfac = P.kA * c.clump / P.a3;
     const T Eb = Ebar * (1.0 / P.a3);
-    SHI = riccati_ne(c.nHI0, c.nH, neHe, r.aH * rfac, P.kG * Eb, P.dt);
+    SHI = riccati_ne(c.nHI0, c.nH, neHe, on_lanes(temp, r.aH) * rfac, P.kG * Eb, P.dt);
     const T rne = ne * rfac;
-    helium_chain(c.nHeI0, c.nHeII0, c.nHe, P.kG1 * Eb, P.kG2 * Eb, r.a2 * rne, r.a3 * rne, P.dt, SHeI, SHeII);
+    helium_chain(c.nHeI0, c.nHeII0, c.nHe, P.kG1 * Eb, P.kG2 * Eb, on_lanes(temp, r.a2) * rne,
+                 on_lanes(temp, r.a3) * rne, P.dt, SHeI, SHeII);
     if (P.isothermal) {
         Se = ec * 0.0;
         return;
@@ -194,8 +210,9 @@ RT_HD void local_solutions_he(const PhysParams& P, const CellHe& c, const T& ec,
     if (cool) {
         const double s = P.un / P.a3;
         const T nep = ne * s, nHIIp = (c.nH - nHI) * s, nHIp = nHI * s, n2p = nHeII * s, n3p = nHeIII * s;
-        const T vol = nep * (r.rf * nHIIp + r.ff * (n2p + 4.0 * n3p) + r.ce * nHIp + r.c2 * n2p + r.c3 * n3p) +
-                      r.comp * nep;
+        const T vol = nep * (on_lanes(temp, r.rf) * nHIIp + on_lanes(temp, r.ff) * (n2p + 4.0 * n3p) +
+                             on_lanes(temp, r.ce) * nHIp + on_lanes(temp, r.c2) * n2p + on_lanes(temp, r.c3) * n3p) +
+                      on_lanes(temp, r.comp) * nep;
         cooling = (P.kC * P.a3 / c.rho) * vol;
     }
     Se = (heat - cooling) * P.phi_e;

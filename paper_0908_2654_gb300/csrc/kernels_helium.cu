@@ -84,6 +84,17 @@ __device__ __forceinline__ void eval_he(const PhysParams& P, const CellHe& c, co
     }
 }
 
+// the local residuals alone (line-search trials)
+template <bool ISO>
+__device__ __forceinline__ void eval_f_he(const PhysParams& P, const CellHe& c, const double (&u)[4], double E,
+                                          double (&f)[4]) {
+    double S[4];
+    local_solutions_he<double>(P, c, u[0], u[1], u[2], u[3], E, S[0], S[1], S[2], S[3]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) f[i] = u[i] - S[i];
+    if (ISO) f[0] = 0.0;
+}
+
 __device__ __forceinline__ double scaled_max(const double (&f)[4], const double (&inv)[4]) {
     return fmax(fmax(fabs(f[0]) * inv[0], fabs(f[1]) * inv[1]), fmax(fabs(f[2]) * inv[2], fabs(f[3]) * inv[3]));
 }
@@ -117,6 +128,7 @@ __device__ __forceinline__ LocalHe local_block_he(const PhysParams& P, const Cel
             b[i][1] = 0.0;
         }
         solve4(a, b);
+        // backtracking on the residuals alone; the Jacobian only at the accepted point
         double lam = 1.0;
         bool moved = false;
         for (int k = 0; k < 40; ++k, lam *= 0.5) {
@@ -125,24 +137,18 @@ __device__ __forceinline__ LocalHe local_block_he(const PhysParams& P, const Cel
             for (int i = 0; i < 4; ++i) ut[i] = u[i] + lam * b[i][0];
             if (ISO) ut[0] = 0.0;
             clamp_he(c, ut);
-            double ft[4], Jt[4][4], JEt[4];
-            eval_he<ISO>(P, c, ut, E, ft, Jt, JEt);
-            const double rt = scaled_max(ft, inv);
-            if (rt < r) {
+            double ft[4];
+            eval_f_he<ISO>(P, c, ut, E, ft);
+            if (scaled_max(ft, inv) < r) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    u[i] = ut[i];
-                    f[i] = ft[i];
-                    JE[i] = JEt[i];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) J[i][j] = Jt[i][j];
-                }
-                r = rt;
+                for (int i = 0; i < 4; ++i) u[i] = ut[i];
                 moved = true;
                 break;
             }
         }
         if (!moved) break;   // round-off floor
+        eval_he<ISO>(P, c, u, E, f, J, JE);
+        r = scaled_max(f, inv);
     }
     double a[4][4], b[4][2];
 #pragma unroll
