@@ -215,8 +215,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_assemble(PhysParams P, AssembleAr
         if (A.vz) v2 += A.vz[i] * A.vz[i];
         const HCell c = make_hcell(P, inv_a3, A.rho[i], A.n0[i], A.E0[i], A.e_h[i] - 0.5 * v2,
                                    A.clump ? (double)A.clump[i] : 1.0);
-        const double se = fmax(c.eh_kin, P.e_floor);
-        const double inv_se = 1.0 / se, inv_rho = 1.0 / c.rho;
+        const double inv_se = 1.0 / fmax(c.eh_kin, P.e_floor), inv_rho = c.inv_rho;
 
         double ec_in = GIVEN ? A.ec_given[i] : (A.ec_guess ? A.ec_guess[i] : 0.0);
         double n_in = GIVEN ? A.n_given[i] : A.n_guess[i];
@@ -236,8 +235,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_assemble(PhysParams P, AssembleAr
         const double dg = AEE - AEn * L.X;
         const double rh = -fE + AEn * L.Y;
 
-        const double wEc = 1.0 / fmax(fmax(fabs(Ec[i]), c.E0), P.E_floor);
-        const double wEt = 1.0 / fmax(fmax(fabs(E), c.E0), P.E_floor);
+        // the norm weights of E at the current iterate and at the trial from one reciprocal
+        const double mEc = fmax(fmax(fabs(Ec[i]), c.E0), P.E_floor);
+        const double mEt = fmax(fmax(fabs(E), c.E0), P.E_floor);
+        const double wcw = 1.0 / (mEc * mEt);
+        const double wEc = mEt * wcw, wEt = mEc * wcw;
         const double loc = (L.fn * inv_rho) * (L.fn * inv_rho) + (L.fe * inv_se) * (L.fe * inv_se);
         acc[0] += (wEc * fE) * (wEc * fE) + loc;
         acc[1] += (wEt * fE) * (wEt * fE) + loc;
