@@ -420,16 +420,23 @@ __host__ __device__ inline void make_plan(const Dims& top, TailPlan& p) {
     p.dense = (last.n() > 1 && last.n() <= kDenseMax) ? 1 : 0;
 }
 
-// one colour of a red-black Gauss-Seidel sweep on a shared-memory level: the new value is
-// (b + sum of the neighbours' couplings) / diag; the cell's own previous value is not read.
-// All new values of the colour are computed before any is stored, so on a periodic axis of odd
-// length (where cells 0 and n-1 share a colour and are neighbours) both see each other's old
-// value and the result does not depend on thread timing; with a proper two-colouring this is
-// the same sweep.  Levels hold at most kTailCellsPerThread * blockDim.x cells.
+// colouring of a shared-memory level for its Gauss-Seidel sweeps (rbpass.cuh)
+__device__ __forceinline__ bool odd_periodic(const Dims& d) {
+    return rbp::odd_periodic(d.nx, d.ny, d.nz, d.per);
+}
+__device__ __forceinline__ int tail_colour(const Dims& d, int ncol, int x, int y, int z) {
+    return rbp::multicolour(d.nx, d.ny, d.nz, d.per, ncol, x, y, z);
+}
+
+// one colour of a multicolour Gauss-Seidel sweep on a shared-memory level: the new value is
+// (b + sum of the neighbours' couplings) / diag; the cell's own previous value is not read.  All
+// new values of the colour are computed before any is stored.  Levels hold at most
+// kTailCellsPerThread * blockDim.x cells.
 constexpr int kTailCellsPerThread = 4;
 
 template <class T>
-__device__ void tail_smooth(const Dims& d, T* diag, T* wx, T* wy, T* wz, T* x, const T* b, int color, bool zero) {
+__device__ void tail_smooth(const Dims& d, T* diag, T* wx, T* wy, T* wz, T* x, const T* b, int ncol, int color,
+                            bool zero) {
     const long long n = d.n();
     const long long sy = d.nx, sz = (long long)d.nx * d.ny;
     T nv[kTailCellsPerThread];
@@ -440,7 +447,7 @@ __device__ void tail_smooth(const Dims& d, T* diag, T* wx, T* wy, T* wz, T* x, c
         if (i >= n) continue;
         int cx, cy, cz;
         cell_coords(i, d.nx, d.ny, cx, cy, cz);
-        if (((cx + cy + cz) & 1) != color) continue;
+        if (tail_colour(d, ncol, cx, cy, cz) != color) continue;
         T num = b[i];
         if (!zero) {
             const long long b0 = i - cx - (long long)cy * sy - (long long)cz * sz;
@@ -464,7 +471,7 @@ __device__ void tail_smooth(const Dims& d, T* diag, T* wx, T* wy, T* wz, T* x, c
         if (i >= n) continue;
         int cx, cy, cz;
         cell_coords(i, d.nx, d.ny, cx, cy, cz);
-        if (((cx + cy + cz) & 1) == color) x[i] = nv[k];
+        if (tail_colour(d, ncol, cx, cy, cz) == color) x[i] = nv[k];
     }
 }
 
@@ -552,12 +559,13 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(Level<T> L, int ncycles, 
             const Dims& d = plan.d[l];
             const int o = plan.off[l];
             const bool zero_start = (l > 0) || (cyc == 0);
-            for (int s = 0; s < nu; ++s) {
-                tail_smooth<T>(d, sdiag + o, swx + o, swy + o, swz + o, sx + o, sb + o, 0, zero_start && s == 0);
-                __syncthreads();
-                tail_smooth<T>(d, sdiag + o, swx + o, swy + o, swz + o, sx + o, sb + o, 1, false);
-                __syncthreads();
-            }
+            const int ncol = odd_periodic(d) ? 3 : 2;
+            for (int s = 0; s < nu; ++s)
+                for (int col = 0; col < ncol; ++col) {
+                    tail_smooth<T>(d, sdiag + o, swx + o, swy + o, swz + o, sx + o, sb + o, ncol, col,
+                                   zero_start && s == 0 && col == 0);
+                    __syncthreads();
+                }
             const Dims& cd = plan.d[l + 1];
             const int co = plan.off[l + 1];
             for (long long I = threadIdx.x; I < cd.n(); I += blockDim.x) {
@@ -600,12 +608,13 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(Level<T> L, int ncycles, 
             }
             __syncthreads();
         } else {
-            for (int s = 0; s < 8 * (ld.nx + ld.ny + ld.nz); ++s) {
-                tail_smooth<T>(ld, sdiag + lo, swx + lo, swy + lo, swz + lo, sx + lo, sb + lo, 0, s == 0);
-                __syncthreads();
-                tail_smooth<T>(ld, sdiag + lo, swx + lo, swy + lo, swz + lo, sx + lo, sb + lo, 1, false);
-                __syncthreads();
-            }
+            const int ncol = odd_periodic(ld) ? 3 : 2;
+            for (int s = 0; s < 8 * (ld.nx + ld.ny + ld.nz); ++s)
+                for (int col = 0; col < ncol; ++col) {
+                    tail_smooth<T>(ld, sdiag + lo, swx + lo, swy + lo, swz + lo, sx + lo, sb + lo, ncol, col,
+                                   s == 0 && col == 0);
+                    __syncthreads();
+                }
         }
         for (int l = last - 1; l >= 0; --l) {
             const Dims& d = plan.d[l];
@@ -625,12 +634,13 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(Level<T> L, int ncycles, 
                 sx[o + i] += w1 * v1 + w2 * v2;
             }
             __syncthreads();
-            for (int s = 0; s < nu; ++s) {
-                tail_smooth<T>(d, sdiag + o, swx + o, swy + o, swz + o, sx + o, sb + o, 1, false);
-                __syncthreads();
-                tail_smooth<T>(d, sdiag + o, swx + o, swy + o, swz + o, sx + o, sb + o, 0, false);
-                __syncthreads();
-            }
+            // post-smoothing takes the colours in reverse order
+            const int ncol = odd_periodic(d) ? 3 : 2;
+            for (int s = 0; s < nu; ++s)
+                for (int col = ncol - 1; col >= 0; --col) {
+                    tail_smooth<T>(d, sdiag + o, swx + o, swy + o, swz + o, sx + o, sb + o, ncol, col, false);
+                    __syncthreads();
+                }
         }
     }
     for (long long i = threadIdx.x; i < n0; i += blockDim.x) L.x[i] = sx[i];

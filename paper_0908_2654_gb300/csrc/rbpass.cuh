@@ -154,6 +154,21 @@ RT_HD void split_pair(int nx, int ny, int nz, const int* per, const T* diag, con
     }
 }
 
+// Colouring of the levels the single-CTA coarse solver sweeps, which may have odd dimensions.
+// With no periodic axis of odd length it is the red-black one, (x + y + z) mod 2 (ncol = 2).  A
+// periodic axis of odd length n puts cells 0 and n-1, which are neighbours, on the same parity;
+// then (ncol = 3) each coordinate maps to c(v) = v mod 2, except c(n-1) = 2 on such an axis, and
+// the colour is (c(x) + c(y) + c(z)) mod 3: neighbours differ in one coordinate, whose c differs
+// by 1 or 2, so no two neighbours share a colour.
+RT_HD bool odd_periodic(int nx, int ny, int nz, const int* per) {
+    return (per[0] && (nx & 1)) || (per[1] && (ny & 1)) || (per[2] && (nz & 1));
+}
+RT_HD int multicolour(int nx, int ny, int nz, const int* per, int ncol, int x, int y, int z) {
+    if (ncol == 2) return (x + y + z) & 1;
+    auto c = [](int v, int n, int p) { return (p && (n & 1) && v == n - 1) ? 2 : (v & 1); };
+    return (c(x, nx, per[0]) + c(y, ny, per[1]) + c(z, nz, per[2])) % 3;
+}
+
 // coarse-cell value of the trilinear cell-centred prolongation at fine cell (x, y, z): weights
 // 3/4 and 1/4 along each axis from the coarse cell holding the fine cell and its neighbour on the
 // fine cell's side (the cell itself at a non-periodic edge); xc colour-split when csplit

@@ -116,4 +116,27 @@ long long prolong_host(int nx, int ny, int nz, const int* per, const double* xc,
                 out[((long long)z * ny + y) * nx + x] = rbp::prolong_at(c.data(), csplit, cnx, cny, cnz, per, x, y, z);
     return g_bad_index;
 }
+// pairs of neighbours (periodic wraps included, a cell that is its own neighbour skipped) that
+// share a colour of the coarse solver's colouring, and the number of colours it uses
+long long colour_conflicts(int nx, int ny, int nz, const int* per, int* ncol_out) {
+    const int ncol = rbp::odd_periodic(nx, ny, nz, per) ? 3 : 2;
+    *ncol_out = ncol;
+    long long bad = 0;
+    const int n[3] = {nx, ny, nz};
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const int c = rbp::multicolour(nx, ny, nz, per, ncol, x, y, z);
+                if (c < 0 || c >= ncol) ++bad;
+                for (int a = 0; a < 3; ++a) {
+                    int v[3] = {x, y, z};
+                    if (v[a] + 1 < n[a]) v[a] += 1;
+                    else if (per[a]) v[a] = 0;
+                    else continue;
+                    if (v[0] == x && v[1] == y && v[2] == z) continue;
+                    if (rbp::multicolour(nx, ny, nz, per, ncol, v[0], v[1], v[2]) == c) ++bad;
+                }
+            }
+    return bad;
+}
 }

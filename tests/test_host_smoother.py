@@ -5,7 +5,8 @@ the first colour from its neighbours' old values, x_i = (b_i + sum_faces w_f x_n
 every cell of the other colour from the new values.  Also: the colour-split index is a bijection,
 the split operator fills every entry, the zero start, each pass setting exactly the cells of its
 colour, every index in range, rows shorter and longer than a block, periodic and reflecting axes;
-and the trilinear cell-centred prolongation of a natural or colour-split coarse vector."""
+the trilinear cell-centred prolongation of a natural or colour-split coarse vector; and the
+coarse solver's colouring, which gives no two neighbours one colour, odd periodic axes included."""
 import ctypes
 import os
 import shutil
@@ -136,3 +137,15 @@ def test_prolongation_is_trilinear(lib, shape, per, csplit):
                            cshape[1], cshape[0], csplit, out.ctypes.data_as(ctypes.c_void_p))
     assert bad == 0
     np.testing.assert_allclose(out, _prolong_reference(xc, shape, per), rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("dims,per", [((8, 6, 4), (1, 1, 1)), ((5, 4, 6), (1, 0, 1)), ((5, 5, 5), (1, 1, 1)),
+                                      ((3, 7, 1), (1, 1, 1)), ((1, 1, 5), (0, 0, 1)), ((7, 3, 9), (0, 0, 0)),
+                                      ((2, 3, 3), (1, 1, 0)), ((9, 1, 1), (1, 0, 0))])
+def test_coarse_colouring_has_no_neighbour_conflict(lib, dims, per):
+    ncol = ctypes.c_int(0)
+    lib.colour_conflicts.restype = ctypes.c_longlong
+    bad = lib.colour_conflicts(*dims, (ctypes.c_int * 3)(*per), ctypes.byref(ncol))
+    assert bad == 0
+    odd_per = any(p and n % 2 for n, p in zip(dims, per))
+    assert ncol.value == (3 if odd_per else 2)
