@@ -206,29 +206,51 @@ __device__ __forceinline__ double pow2_scale(double amax, bool inverse) {
     if (amax > 0.0 && isfinite(amax)) frexp(amax, &e);   // amax < 2^e
     return ldexp(1.0, inverse ? e : -e);
 }
-// level-0 vectors in the multigrid's storage order (colour-split when `split`): thread per
-// natural cell, scaled by 2^-e (2^e >= *amax) on the way in and 2^e on the way out
+// level-0 vectors in the multigrid's storage order, scaled by 2^-e (2^e >= *amax) on the way in
+// and by 2^e on the way out (no scaling when amax is null).  Natural order: thread per cell.
 template <class Tin, class Tout>
-__global__ void k_to_level(Dims d, int split, const Tin* __restrict__ a, Tout* __restrict__ out,
-                           const double* __restrict__ amax) {
+__global__ void k_to_level(Dims d, const Tin* __restrict__ a, Tout* __restrict__ out, const double* __restrict__ amax) {
     const double sc = amax ? pow2_scale(*amax, false) : 1.0;
     const long long n = d.n();
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int x, y, z;
-        cell_coords(i, d.nx, d.ny, x, y, z);
-        out[rbp::level_index(split, d.nx, d.ny, d.nz, x, y, z)] = (Tout)((double)a[i] * sc);
-    }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (Tout)((double)a[i] * sc);
 }
 template <class Tin, class Tout>
-__global__ void k_from_level(Dims d, int split, const Tin* __restrict__ a, Tout* __restrict__ out,
+__global__ void k_from_level(Dims d, const Tin* __restrict__ a, Tout* __restrict__ out,
                              const double* __restrict__ amax) {
     const double sc = amax ? pow2_scale(*amax, true) : 1.0;
     const long long n = d.n();
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int x, y, z;
-        cell_coords(i, d.nx, d.ny, x, y, z);
-        out[i] = (Tout)((double)a[rbp::level_index(split, d.nx, d.ny, d.nz, x, y, z)] * sc);
-    }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (Tout)((double)a[i] * sc);
+}
+// Colour-split order: thread per x-pair (one 16-byte load or store of the FP64 pair, one element
+// into or out of each colour half), launched in pass_grid's shape so that no index is divided
+template <class Tout>
+__global__ void __launch_bounds__(rbp::kPairs) k_to_split(Dims d, int rows, const double* __restrict__ a,
+                                                          Tout* __restrict__ out, const double* __restrict__ amax) {
+    int px, y, z;
+    if (!rbp::grid_pair(d.nx, d.ny, rows, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, px, y, z)) return;
+    const double sc = amax ? pow2_scale(*amax, false) : 1.0;
+    const long long hx = d.nx >> 1, half = hx * d.ny * d.nz;
+    const long long m = ((long long)z * d.ny + y) * hx + px;
+    const int c0 = (y + z) & 1;   // colour of the pair's even-x cell
+    const double2 v = reinterpret_cast<const double2*>(a)[m];
+    out[c0 * half + m] = (Tout)(v.x * sc);
+    out[(1 - c0) * half + m] = (Tout)(v.y * sc);
+}
+template <class Tin>
+__global__ void __launch_bounds__(rbp::kPairs) k_from_split(Dims d, int rows, const Tin* __restrict__ a,
+                                                            double* __restrict__ out, const double* __restrict__ amax) {
+    int px, y, z;
+    if (!rbp::grid_pair(d.nx, d.ny, rows, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, px, y, z)) return;
+    const double sc = amax ? pow2_scale(*amax, true) : 1.0;
+    const long long hx = d.nx >> 1, half = hx * d.ny * d.nz;
+    const long long m = ((long long)z * d.ny + y) * hx + px;
+    const int c0 = (y + z) & 1;
+    double2 v;
+    v.x = (double)a[c0 * half + m] * sc;
+    v.y = (double)a[(1 - c0) * half + m] * sc;
+    reinterpret_cast<double2*>(out)[m] = v;
 }
 __global__ void k_cast_f2d(long long n, const float* __restrict__ a, double* __restrict__ b) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -281,23 +303,18 @@ __global__ void __launch_bounds__(kBlock) k_split_level(Level<T> L) {
 }
 
 // x += P xc: trilinear cell-centred prolongation of the coarse correction; thread per fine pair
-// (both cells share the coarse cell and one store into each colour half)
+// (both cells lie in one coarse cell, rbp::prolong_pair), launched in pass_grid's shape
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_prolong_add(Level<T> c, Level<T> f) {
-    const Dims fd = f.d;
-    const int hx = fd.nx >> 1;
-    const long long half = fd.n() / 2;
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < half; m += (long long)gridDim.x * blockDim.x) {
-        const long long r = m / hx;
-        const int px = (int)(m - r * hx);
-        const int z = (int)(r / fd.ny), y = (int)(r - (long long)z * fd.ny);
-#pragma unroll
-        for (int o = 0; o < 2; ++o) {
-            const int x = 2 * px + o;
-            f.x[(long long)((x + y + z) & 1) * half + m] +=
-                rbp::prolong_at(c.x, c.split, c.d.nx, c.d.ny, c.d.nz, c.d.per, x, y, z);
-        }
-    }
+__global__ void __launch_bounds__(rbp::kPairs) k_prolong_add(Level<T> c, Level<T> f, int rows) {
+    int px, y, z;
+    if (!rbp::grid_pair(f.d.nx, f.d.ny, rows, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, px, y, z)) return;
+    const long long hx = f.d.nx >> 1, half = hx * f.d.ny * f.d.nz;
+    const long long m = ((long long)z * f.d.ny + y) * hx + px;
+    const int c0 = (y + z) & 1;   // colour of the even-x cell
+    T v0, v1;
+    rbp::prolong_pair(c.x, c.split, c.d.nx, c.d.ny, c.d.nz, c.d.per, px, y, z, v0, v1);
+    f.x[c0 * half + m] += v0;
+    f.x[(1 - c0) * half + m] += v1;
 }
 
 // b - S x at fine cell (x, y, z) of a colour-split level (operator in natural order)
@@ -685,11 +702,23 @@ void launch_cast_f2d(long long n, const float* a, double* b, cudaStream_t s) {
 }
 template <class Tin, class Tout>
 void launch_to_level(const Dims& d, int split, const Tin* a, Tout* out, const double* amax, cudaStream_t s) {
-    k_to_level<Tin, Tout><<<grid_for(d.n()), kBlock, 0, s>>>(d, split, a, out, amax);
+    if (split) {
+        int gx, gy, gz, rows;
+        rbp::pass_grid(d.nx, d.ny, d.nz, gx, gy, gz, rows);
+        k_to_split<Tout><<<dim3(gx, gy, gz), rbp::kPairs, 0, s>>>(d, rows, a, out, amax);
+    } else {
+        k_to_level<Tin, Tout><<<grid_for(d.n()), kBlock, 0, s>>>(d, a, out, amax);
+    }
 }
 template <class Tin, class Tout>
 void launch_from_level(const Dims& d, int split, const Tin* a, Tout* out, const double* amax, cudaStream_t s) {
-    k_from_level<Tin, Tout><<<grid_for(d.n()), kBlock, 0, s>>>(d, split, a, out, amax);
+    if (split) {
+        int gx, gy, gz, rows;
+        rbp::pass_grid(d.nx, d.ny, d.nz, gx, gy, gz, rows);
+        k_from_split<Tin><<<dim3(gx, gy, gz), rbp::kPairs, 0, s>>>(d, rows, a, out, amax);
+    } else {
+        k_from_level<Tin, Tout><<<grid_for(d.n()), kBlock, 0, s>>>(d, a, out, amax);
+    }
 }
 template void launch_to_level<double, float>(const Dims&, int, const double*, float*, const double*, cudaStream_t);
 template void launch_to_level<double, double>(const Dims&, int, const double*, double*, const double*, cudaStream_t);
@@ -751,7 +780,9 @@ int launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, cudaStrea
 
 template <class T>
 void launch_prolong_add(const Level<T>& c, const Level<T>& f, cudaStream_t s) {
-    k_prolong_add<T><<<grid_for(f.d.n() / 2), kBlock, 0, s>>>(c, f);
+    int gx, gy, gz, rows;
+    rbp::pass_grid(f.d.nx, f.d.ny, f.d.nz, gx, gy, gz, rows);
+    k_prolong_add<T><<<dim3(gx, gy, gz), rbp::kPairs, 0, s>>>(c, f, rows);
 }
 
 template <class T>

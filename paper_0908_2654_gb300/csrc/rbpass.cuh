@@ -58,22 +58,29 @@ struct Pass {
     int rows;       // rows per block: kPairs / pairs per row (at least 1)
 };
 
-// the thread of block (bx, by, bz) and lane t: pair px of row y, plane z; returns false when
-// it has no cell
-template <class T>
-RT_HD bool pair_cell(const Pass<T>& A, int bx, int by, int bz, int t, int& x, int& y, int& z) {
-    const int hp = A.nx >> 1;
-    int px, ry;
-    if (A.rows == 1) {
+// the pair of the thread of block (bx, by, bz) and lane t in a launch of pass_grid's shape: pair
+// px of row y, plane bz; returns false when it has none
+RT_HD bool grid_pair(int nx, int ny, int rows, int bx, int by, int bz, int t, int& px, int& y, int& z) {
+    const int hp = nx >> 1;
+    int ry;
+    if (rows == 1) {
         px = bx * kPairs + t;
         ry = 0;
     } else {
         ry = t / hp;
         px = t - ry * hp;
     }
-    y = by * A.rows + ry;
-    z = A.rev ? A.nz - 1 - bz : bz;
-    if (px >= hp || y >= A.ny || ry >= A.rows) return false;
+    y = by * rows + ry;
+    z = bz;
+    return px < hp && y < ny && ry < rows;
+}
+
+// the cell of the pass's colour in the pair of block (bx, by, bz) and lane t (planes in reverse
+// when A.rev); returns false when there is none
+template <class T>
+RT_HD bool pair_cell(const Pass<T>& A, int bx, int by, int bz, int t, int& x, int& y, int& z) {
+    int px;
+    if (!grid_pair(A.nx, A.ny, A.rows, bx, by, A.rev ? A.nz - 1 - bz : bz, t, px, y, z)) return false;
     x = 2 * px + ((y + z + A.colour) & 1);   // the pair's cell of this colour
     return true;
 }
@@ -192,6 +199,35 @@ RT_HD T prolong_at(const T* xc, int csplit, int cnx, int cny, int cnz, const int
     const T v1 = w1 * (w1 * C(X, Y, Z) + w2 * C(X2, Y, Z)) + w2 * (w1 * C(X, Y2, Z) + w2 * C(X2, Y2, Z));
     const T v2 = w1 * (w1 * C(X, Y, Z2) + w2 * C(X2, Y, Z2)) + w2 * (w1 * C(X, Y2, Z2) + w2 * C(X2, Y2, Z2));
     return w1 * v1 + w2 * v2;
+}
+
+// prolong_at for both cells of fine pair (2 px, 2 px + 1), which lie in coarse cell px and take
+// their x-neighbour from coarse cells px - 1 and px + 1: twelve coarse values instead of sixteen
+template <class T>
+RT_HD void prolong_pair(const T* xc, int csplit, int cnx, int cny, int cnz, const int* per, int px, int y, int z,
+                        T& v0, T& v1) {
+    const int Y = y >> 1, Z = z >> 1;
+    auto other = [](int C, int odd, int n, int p) {
+        const int c = odd ? C + 1 : C - 1;
+        if (c >= 0 && c < n) return c;
+        return p ? (c < 0 ? c + n : c - n) : C;
+    };
+    const int Xm = other(px, 0, cnx, per[0]), Xp = other(px, 1, cnx, per[0]);
+    const int Y2 = other(Y, y & 1, cny, per[1]);
+    const int Z2 = other(Z, z & 1, cnz, per[2]);
+    auto C = [&](int a, int b, int e) {
+        const long long j = level_index(csplit, cnx, cny, cnz, a, b, e);
+        RT_SWEEP_CHECK(j >= 0 && j < (long long)cnx * cny * cnz);
+        return xc[j];
+    };
+    const T w1 = T(0.75), w2 = T(0.25);
+    // y-z weighted columns at coarse x = px - 1, px, px + 1
+    auto col = [&](int a) {
+        return w1 * (w1 * C(a, Y, Z) + w2 * C(a, Y2, Z)) + w2 * (w1 * C(a, Y, Z2) + w2 * C(a, Y2, Z2));
+    };
+    const T cm = col(Xm), c0 = col(px), cp = col(Xp);
+    v0 = w1 * c0 + w2 * cm;
+    v1 = w1 * c0 + w2 * cp;
 }
 
 }  // namespace rbp

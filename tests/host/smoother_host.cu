@@ -116,6 +116,27 @@ long long prolong_host(int nx, int ny, int nz, const int* per, const double* xc,
                 out[((long long)z * ny + y) * nx + x] = rbp::prolong_at(c.data(), csplit, cnx, cny, cnz, per, x, y, z);
     return g_bad_index;
 }
+// the same from prolong_pair, one fine x-pair at a time (nx even)
+long long prolong_pair_host(int nx, int ny, int nz, const int* per, const double* xc, int cnx, int cny, int cnz,
+                            int csplit, double* out) {
+    g_bad_index = 0;
+    const long long nc = (long long)cnx * cny * cnz;
+    std::vector<double> c(nc);
+    for (int Z = 0; Z < cnz; ++Z)
+        for (int Y = 0; Y < cny; ++Y)
+            for (int X = 0; X < cnx; ++X)
+                c[rbp::level_index(csplit, cnx, cny, cnz, X, Y, Z)] = xc[((long long)Z * cny + Y) * cnx + X];
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int px = 0; px < nx / 2; ++px) {
+                double v0, v1;
+                rbp::prolong_pair(c.data(), csplit, cnx, cny, cnz, per, px, y, z, v0, v1);
+                out[((long long)z * ny + y) * nx + 2 * px] = v0;
+                out[((long long)z * ny + y) * nx + 2 * px + 1] = v1;
+            }
+    return g_bad_index;
+}
+
 // pairs of neighbours (periodic wraps included, a cell that is its own neighbour skipped) that
 // share a colour of the coarse solver's colouring, and the number of colours it uses
 long long colour_conflicts(int nx, int ny, int nz, const int* per, int* ncol_out) {

@@ -125,15 +125,17 @@ def test_sweep_equals_red_black_gauss_seidel(lib, shape, per, dtype):
         np.testing.assert_allclose(got, ref, rtol=tol, atol=tol * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("fn", ["prolong_host", "prolong_pair_host"])
 @pytest.mark.parametrize("csplit", [0, 1])
-@pytest.mark.parametrize("shape,per", [CASES[0], CASES[1], CASES[3], ((40, 24, 48), (False, False, True))])
-def test_prolongation_is_trilinear(lib, shape, per, csplit):
+@pytest.mark.parametrize("shape,per", [CASES[0], CASES[1], CASES[3], ((40, 24, 48), (False, False, True)),
+                                       ((4, 2, 2), (True, True, True))])
+def test_prolongation_is_trilinear(lib, shape, per, csplit, fn):
     rng = np.random.default_rng(7)
     cshape = tuple(n // 2 for n in shape)
     xc = rng.standard_normal(cshape)
     nz, ny, nx = shape
     out = np.zeros(shape)
-    bad = lib.prolong_host(nx, ny, nz, (ctypes.c_int * 3)(*per), xc.ctypes.data_as(ctypes.c_void_p), cshape[2],
+    bad = getattr(lib, fn)(nx, ny, nz, (ctypes.c_int * 3)(*per), xc.ctypes.data_as(ctypes.c_void_p), cshape[2],
                            cshape[1], cshape[0], csplit, out.ctypes.data_as(ctypes.c_void_p))
     assert bad == 0
     np.testing.assert_allclose(out, _prolong_reference(xc, shape, per), rtol=1e-14, atol=1e-14)
