@@ -7,11 +7,13 @@ namespace cellgrid {
 
 constexpr int kBlock = 256;
 
+// (x, y, z) of cell i = (z ny + y) nx + x.  Grids hold at most 2^31 cells (rt_init_grid), so
+// i fits 32 bits and the divisions are 32-bit ones (a 64-bit division is several times longer).
 __device__ __forceinline__ void cell_coords(long long i, int nx, int ny, int& x, int& y, int& z) {
-    long long q = i / nx;
-    x = (int)(i - q * nx);
-    z = (int)(q / ny);
-    y = (int)(q - (long long)z * ny);
+    const unsigned u = (unsigned)i, q = u / (unsigned)nx;
+    x = (int)(u - q * (unsigned)nx);
+    z = (int)(q / (unsigned)ny);
+    y = (int)(q - (unsigned)z * (unsigned)ny);
 }
 
 // neighbour index along an axis; at a wall the index is clamped (its face coupling is 0)

@@ -13,6 +13,7 @@
 // with J_X taken in gather form: each cell collects the contributions of its own rows and of the
 // six face terms it shares with its neighbours (the face coefficient D is differentiated with
 // respect to the starting state it is evaluated from).
+#include "cellgrid.cuh"
 #include "kernels.cuh"
 
 namespace {
@@ -27,14 +28,9 @@ int grid_for(long long n) {
     return (int)b;
 }
 
-__device__ __forceinline__ void cell_coords(long long i, int nx, int ny, int& x, int& y, int& z) {
-    long long q = i / nx;
-    x = (int)(i - q * nx);
-    z = (int)(q / ny);
-    y = (int)(q - (long long)z * ny);
-}
-__device__ __forceinline__ int up(int c, int n, int per) { return c + 1 < n ? c + 1 : (per ? 0 : c); }
-__device__ __forceinline__ int dn(int c, int n, int per) { return c > 0 ? c - 1 : (per ? n - 1 : c); }
+using cellgrid::cell_coords;
+using cellgrid::dn;
+using cellgrid::up;
 
 __device__ __forceinline__ CellIn cell_in(const AdjointArgs& A, long long i) {
     CellIn c;

@@ -16,6 +16,7 @@
 //        coefficients);
 //      - a single-CTA solver that runs the remaining coarse levels in shared memory and finishes
 //        with a dense Cholesky solve (or the exact 1-cell solve) on the coarsest one.
+#include "cellgrid.cuh"
 #include "kernels.cuh"
 #include "rbpass.cuh"
 
@@ -31,14 +32,9 @@ int grid_for(long long n) {
     return (int)b;
 }
 
-__device__ __forceinline__ void cell_coords(long long i, int nx, int ny, int& x, int& y, int& z) {
-    long long q = i / nx;
-    x = (int)(i - q * nx);
-    z = (int)(q / ny);
-    y = (int)(q - (long long)z * ny);
-}
-__device__ __forceinline__ int up(int c, int n, int per) { return c + 1 < n ? c + 1 : (per ? 0 : c); }
-__device__ __forceinline__ int dn(int c, int n, int per) { return c > 0 ? c - 1 : (per ? n - 1 : c); }
+using cellgrid::cell_coords;
+using cellgrid::dn;
+using cellgrid::up;
 
 // block partials of NS sums followed by NM maxima (slot k at partials[k * gridDim.x + block])
 template <int NS, int NM>
