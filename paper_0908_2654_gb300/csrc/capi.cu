@@ -251,7 +251,7 @@ void harvest(rt_grid* g) {
 enum HierarchyStatus { HIER_OK = 0, HIER_ODD, HIER_NOMEM };
 
 // lv[0] takes diag0 (freed with the grid) whatever the outcome.  Every level but the last is
-// smoothed and gets the colour-split copy of its operator (ds, w6).
+// smoothed and gets the colour-split copy of its operator (dinv, w6).
 template <class T>
 HierarchyStatus build_hierarchy(rt_grid* g, Hierarchy<T>& H, T* diag0, T* wx0, T* wy0, T* wz0) {
     bool ok = true;
@@ -287,9 +287,9 @@ HierarchyStatus build_hierarchy(rt_grid* g, Hierarchy<T>& H, T* diag0, T* wx0, T
         Level<T>& s = H.lv[l];
         const size_t n = (size_t)s.d.n();
         s.split = 1;
-        s.ds = dalloc<T>(n, ok);
+        s.dinv = dalloc<T>(n, ok);
         s.w6 = dalloc<T>(3 * n, ok);
-        H.owned.push_back(s.ds);
+        H.owned.push_back(s.dinv);
         H.owned.push_back(s.w6);
         if (!ok) return HIER_NOMEM;
     }

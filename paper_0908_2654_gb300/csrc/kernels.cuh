@@ -195,7 +195,7 @@ struct Level {
     T* wx;
     T* wy;
     T* wz;
-    T* ds;     // colour-split diagonal (split levels)
+    T* dinv;   // colour-split inverse diagonal (split levels)
     T* w6;     // six face arrays of the colour-0 cells, n/2 each (split levels)
     T* x;      // current iterate
     T* b;
@@ -203,7 +203,7 @@ struct Level {
 };
 template <class T>
 void launch_coarsen(const Level<T>& f, const Level<T>& c, cudaStream_t s);
-// ds and w6 of a split level from its natural-order operator
+// dinv and w6 of a split level from its natural-order operator
 template <class T>
 void launch_split_level(const Level<T>& L, cudaStream_t s);
 // one red-black Gauss-Seidel sweep of a split level's x in place as two colour passes

@@ -282,12 +282,10 @@ __global__ void k_cg_scalars(double* scal, const double* dots, int phase) {
 
 // one colour pass (colour C) of a red-black sweep of a colour-split level in place (rbpass.cuh)
 template <int C, class T>
-__global__ void __launch_bounds__(rbp::kPairs) k_rbgs_pass(rbp::Pass<T> A) {
+__global__ void __launch_bounds__(rbp::kPairs, 16) k_rbgs_pass(rbp::Pass<T> A) {
     int x, y, z;
     if (!rbp::pair_cell(A, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, x, y, z)) return;
-    const long long half = (long long)(A.nx >> 1) * A.ny * A.nz;
-    const long long m = ((long long)z * A.ny + y) * (A.nx >> 1) + (x >> 1);
-    A.x[C * half + m] = rbp::cell_value<C>(A, x, y, z);
+    A.x[rbp::pair_of(A, x, y, z)] = rbp::cell_value<C>(A, x, y, z);
 }
 
 // the smoother's copy of a level's operator (colour-split diagonal, colour-0 face arrays)
@@ -295,7 +293,7 @@ template <class T>
 __global__ void __launch_bounds__(kBlock) k_split_level(Level<T> L) {
     const long long half = L.d.n() / 2;
     for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < half; m += (long long)gridDim.x * blockDim.x)
-        rbp::split_pair(L.d.nx, L.d.ny, L.d.nz, L.d.per, L.diag, L.wx, L.wy, L.wz, m, L.ds, L.w6);
+        rbp::split_pair(L.d.nx, L.d.ny, L.d.nz, L.d.per, L.diag, L.wx, L.wy, L.wz, m, L.dinv, L.w6);
 }
 
 // x += P xc: trilinear cell-centred prolongation of the coarse correction; thread per fine pair
@@ -751,22 +749,14 @@ template <class T>
 int launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, cudaStream_t s) {
     const Dims& d = L.d;
     for (int pass = 0; pass < 2; ++pass) {
-        rbp::Pass<T> A;
-        A.nx = d.nx;
-        A.ny = d.ny;
-        A.nz = d.nz;
-        for (int k = 0; k < 3; ++k) A.per[k] = d.per[k];
-        A.ds = L.ds;
-        A.w6 = L.w6;
-        A.b = L.b;
-        A.x = L.x;
-        A.colour = pass == 0 ? first : 1 - first;
-        A.zero = pass == 0 && zero_guess;
-        A.rev = pass;   // the second pass starts on the planes the first read last
-        int gx, gy, gz;
-        rbp::pass_grid(d.nx, d.ny, d.nz, gx, gy, gz, A.rows);
+        const int colour = pass == 0 ? first : 1 - first;
+        // the second pass starts on the planes the first read last
+        const rbp::Pass<T> A = rbp::make_pass<T>(d.nx, d.ny, d.nz, d.per, L.w6, L.dinv, L.b, L.x, colour,
+                                                 pass == 0 && zero_guess, pass);
+        int gx, gy, gz, rows;
+        rbp::pass_grid(d.nx, d.ny, d.nz, gx, gy, gz, rows);
         const dim3 grid(gx, gy, gz);
-        if (A.colour == 0)
+        if (colour == 0)
             k_rbgs_pass<0, T><<<grid, rbp::kPairs, 0, s>>>(A);
         else
             k_rbgs_pass<1, T><<<grid, rbp::kPairs, 0, s>>>(A);

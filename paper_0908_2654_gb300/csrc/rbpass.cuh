@@ -12,7 +12,7 @@
 // (face arrays of n/2 each, in the order -x, +x, -y, +y, -z, +z).  A colour pass then streams
 // contiguous arrays only: its own half of b and the diagonal, all six face arrays, the other
 // colour's half of x (neighbours at pair offsets 0, +-1, +-nx/2, +-nx ny/2) and its own half of x
-// written: 5 words per cell of the level per pass.  In natural order a pass over one colour moves
+// written: 5 words per cell of the level per pass (the diagonal is stored inverted).  In natural order a pass over one colour moves
 // every sector of b, diag, x, wx, wy, wz (half of each used) and rewrites half of x: about 7.
 //
 // A pass is one kernel launch with one thread per pair, a block per row segment and plane, and no
@@ -44,19 +44,60 @@ RT_HD long long level_index(int split, int nx, int ny, int nz, int x, int y, int
     return (long long)((x + y + z) & 1) * half + (i >> 1);
 }
 
+// launch geometry of a pass: (blocks per row, row blocks, planes)
+inline void pass_grid(int nx, int ny, int nz, int& gx, int& gy, int& gz, int& rows) {
+    const int hp = nx / 2;
+    if (hp >= kPairs) {
+        rows = 1;
+        gx = (hp + kPairs - 1) / kPairs;
+    } else {
+        rows = kPairs / hp;
+        gx = 1;
+    }
+    gy = (ny + rows - 1) / rows;
+    gz = nz;
+}
+
+// One colour pass.  The host points each array at the half (or face array) the pass uses, so the
+// kernel indexes with the pair number alone: a level holds at most 2^31 cells, so every pair
+// number and neighbour pair number fits in an int.
 template <class T>
 struct Pass {
     int nx, ny, nz;
     int per[3];
-    const T* ds;    // diagonal, colour-split
-    const T* w6;    // six face arrays of the colour-0 cells
-    const T* b;     // colour-split
-    T* x;           // colour-split, updated in place
+    const T* w[6];  // face arrays of the colour-0 cells, -x, +x, -y, +y, -z, +z
+    const T* dinv;  // 1 / diagonal over this colour's half
+    const T* b;     // this colour's half of b
+    const T* xo;    // the other colour's half of x (read)
+    T* x;           // this colour's half of x (written)
     int colour;     // parity of the cells this pass sets
     int zero;       // the old iterate is zero (first pass of a sweep from zero)
     int rev;        // blocks take the planes from the last to the first
     int rows;       // rows per block: kPairs / pairs per row (at least 1)
 };
+
+// the pass over level arrays x, b (colour-split), dinv (colour-split) and w6 (six face arrays)
+template <class T>
+RT_HD Pass<T> make_pass(int nx, int ny, int nz, const int* per, const T* w6, const T* dinv, const T* b, T* x,
+                        int colour, int zero, int rev) {
+    Pass<T> A;
+    const long long half = (long long)nx * ny * nz / 2;
+    A.nx = nx;
+    A.ny = ny;
+    A.nz = nz;
+    for (int k = 0; k < 3; ++k) A.per[k] = per[k];
+    for (int f = 0; f < 6; ++f) A.w[f] = w6 + f * half;
+    A.dinv = dinv + colour * half;
+    A.b = b + colour * half;
+    A.xo = x + (1 - colour) * half;
+    A.x = x + colour * half;
+    A.colour = colour;
+    A.zero = zero;
+    A.rev = rev;
+    int gx, gy, gz;
+    pass_grid(nx, ny, nz, gx, gy, gz, A.rows);
+    return A;
+}
 
 // the pair of the thread of block (bx, by, bz) and lane t in a launch of pass_grid's shape: pair
 // px of row y, plane bz; returns false when it has none
@@ -88,8 +129,8 @@ RT_HD bool pair_cell(const Pass<T>& A, int bx, int by, int bz, int t, int& x, in
 // neighbour pairs of cell (x, y, z) (pair m) in face order; -1 across a non-periodic boundary.
 // The neighbour across face f has the other colour; for a colour-1 cell the coupling of face f
 // is the opposite face (f ^ 1) of that colour-0 neighbour.
-RT_HD void neighbour_pairs(int nx, int ny, int nz, const int* per, int x, int y, int z, long long m, long long* q) {
-    const long long hx = nx >> 1, hxy = hx * ny, half = hxy * nz;
+RT_HD void neighbour_pairs(int nx, int ny, int nz, const int* per, int x, int y, int z, int m, int* q) {
+    const int hx = nx >> 1, hxy = hx * ny, half = hxy * nz;
     const int odd = x & 1;
     q[FXM] = odd ? m : (x > 0 ? m - 1 : (per[0] ? m - 1 + hx : -1));
     q[FXP] = !odd ? m : (x + 1 < nx ? m + 1 : (per[0] ? m + 1 - hx : -1));
@@ -99,48 +140,37 @@ RT_HD void neighbour_pairs(int nx, int ny, int nz, const int* per, int x, int y,
     q[FZP] = z + 1 < nz ? m + hxy : (per[2] ? m + hxy - half : -1);
 }
 
+// pair number of cell (x, y, z)
+template <class T>
+RT_HD int pair_of(const Pass<T>& A, int x, int y, int z) {
+    return (z * A.ny + y) * (A.nx >> 1) + (x >> 1);
+}
+
 // new value of cell (x, y, z) of colour C from its neighbours
 template <int C, class T>
 RT_HD T cell_value(const Pass<T>& A, int x, int y, int z) {
-    const long long hx = A.nx >> 1, half = hx * A.ny * A.nz;
-    const long long m = ((long long)z * A.ny + y) * hx + (x >> 1);
-    RT_SWEEP_CHECK(m >= 0 && m < half);
-    const long long own = C * half + m;
-    T num = A.b[own];
+    const int m = pair_of(A, x, y, z);
+    RT_SWEEP_CHECK(m >= 0 && (long long)m < (long long)A.nx * A.ny * A.nz / 2);
+    T num = A.b[m];
     if (!A.zero) {
-        const T* xo = A.x + (1 - C) * half;
-        long long q[6];
+        int q[6];
         neighbour_pairs(A.nx, A.ny, A.nz, A.per, x, y, z, m, q);
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
             if (q[f] < 0) continue;
-            RT_SWEEP_CHECK(q[f] < half);
-            const T w = C == 0 ? A.w6[f * half + m] : A.w6[(f ^ 1) * half + q[f]];
-            num += w * xo[q[f]];
+            RT_SWEEP_CHECK((long long)q[f] < (long long)A.nx * A.ny * A.nz / 2);
+            const T w = C == 0 ? A.w[f][m] : A.w[f ^ 1][q[f]];
+            num += w * A.xo[q[f]];
         }
     }
-    return num / A.ds[own];
+    return num * A.dinv[m];
 }
 
-// launch geometry of a pass: (blocks per row, row blocks, planes)
-inline void pass_grid(int nx, int ny, int nz, int& gx, int& gy, int& gz, int& rows) {
-    const int hp = nx / 2;
-    if (hp >= kPairs) {
-        rows = 1;
-        gx = (hp + kPairs - 1) / kPairs;
-    } else {
-        rows = kPairs / hp;
-        gx = 1;
-    }
-    gy = (ny + rows - 1) / rows;
-    gz = nz;
-}
-
-// colour-split diagonal and colour-0 face arrays of pair m from the natural diagonal and the
-// couplings on each cell's +x/+y/+z face (zero on a non-periodic boundary face)
+// colour-split inverse diagonal and colour-0 face arrays of pair m from the natural diagonal and
+// the couplings on each cell's +x/+y/+z face (zero on a non-periodic boundary face)
 template <class T>
 RT_HD void split_pair(int nx, int ny, int nz, const int* per, const T* diag, const T* wx, const T* wy, const T* wz,
-                      long long m, T* ds, T* w6) {
+                      long long m, T* dinv, T* w6) {
     const long long hx = nx >> 1, half = hx * ny * nz;
     const long long r = m / hx;
     const int px = (int)(m - r * hx), y = (int)(r % ny), z = (int)(r / ny);
@@ -150,7 +180,7 @@ RT_HD void split_pair(int nx, int ny, int nz, const int* per, const T* diag, con
         const long long i = 2 * m + o;
         RT_SWEEP_CHECK(i >= 0 && i < sv);
         const int c = (x + y + z) & 1;
-        ds[c * half + m] = diag[i];
+        dinv[c * half + m] = T(1) / diag[i];
         if (c) continue;
         w6[FXM * half + m] = x > 0 ? wx[i - 1] : (per[0] ? wx[i - 1 + nx] : T(0));
         w6[FXP * half + m] = x + 1 < nx || per[0] ? wx[i] : T(0);

@@ -22,8 +22,8 @@ static long long run_sweep(int nx, int ny, int nz, const int* per, const T* diag
     g_bad_index = 0;
     const long long n = (long long)nx * ny * nz, half = n / 2;
     // the level in colour-split storage
-    std::vector<T> ds(n, T(-1)), w6(3 * n, T(-1)), bs(n), xs(n);
-    for (long long m = 0; m < half; ++m) rbp::split_pair(nx, ny, nz, per, diag, wx, wy, wz, m, ds.data(), w6.data());
+    std::vector<T> dinv(n, T(-1)), w6(3 * n, T(-1)), bs(n), xs(n);
+    for (long long m = 0; m < half; ++m) rbp::split_pair(nx, ny, nz, per, diag, wx, wy, wz, m, dinv.data(), w6.data());
     std::vector<int> seen(n, 0);
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
@@ -41,24 +41,15 @@ static long long run_sweep(int nx, int ny, int nz, const int* per, const T* diag
     for (long long s = 0; s < n; ++s)
         if (seen[s] != 1) ++g_bad_index;   // level_index is a bijection
     for (long long k = 0; k < n; ++k)
-        if (ds[k] == T(-1)) ++g_bad_index;   // every diagonal entry written
+        if (dinv[k] == T(-1)) ++g_bad_index;   // every diagonal entry written
     for (long long k = 0; k < 3 * n; ++k)
         if (w6[k] == T(-1)) ++g_bad_index;   // every face entry written
     for (int pass = 0; pass < 2; ++pass) {
-        rbp::Pass<T> A;
-        A.nx = nx;
-        A.ny = ny;
-        A.nz = nz;
-        for (int q = 0; q < 3; ++q) A.per[q] = per[q];
-        A.ds = ds.data();
-        A.w6 = w6.data();
-        A.b = bs.data();
-        A.x = xs.data();
-        A.colour = pass == 0 ? first : 1 - first;
-        A.zero = pass == 0 && zero;
-        A.rev = pass;
-        int gx, gy, gz;
-        rbp::pass_grid(nx, ny, nz, gx, gy, gz, A.rows);
+        const int colour = pass == 0 ? first : 1 - first;
+        const rbp::Pass<T> A = rbp::make_pass<T>(nx, ny, nz, per, w6.data(), dinv.data(), bs.data(), xs.data(), colour,
+                                                 pass == 0 && zero, pass);
+        int gx, gy, gz, rows;
+        rbp::pass_grid(nx, ny, nz, gx, gy, gz, rows);
         std::vector<int> hits(n, 0);
         // a pass never reads the cells it sets, so the order of its threads does not matter
         for (int bz = 0; bz < gz; ++bz)
@@ -72,8 +63,10 @@ static long long run_sweep(int nx, int ny, int nz, const int* per, const T* diag
                             continue;
                         }
                         const long long s = rbp::level_index(1, nx, ny, nz, cx, cy, cz);
+                        if (s != A.colour * half + rbp::pair_of(A, cx, cy, cz)) ++g_bad_index;
                         ++hits[((long long)cz * ny + cy) * nx + cx];
-                        xs[s] = A.colour ? rbp::cell_value<1>(A, cx, cy, cz) : rbp::cell_value<0>(A, cx, cy, cz);
+                        A.x[rbp::pair_of(A, cx, cy, cz)] =
+                            A.colour ? rbp::cell_value<1>(A, cx, cy, cz) : rbp::cell_value<0>(A, cx, cy, cz);
                     }
         // every cell of the pass's colour set exactly once, no other cell touched
         for (int z = 0; z < nz; ++z)
