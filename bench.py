@@ -73,13 +73,14 @@ def l2_note(n):
     return f"inputs smaller than L2 at this size (one Newton evaluation moves {ws / 1e6:.0f} MB); L2 not flushed"
 
 
-# FP64 flops per cell of one newton_assemble launch on this workload (mean over the five
-# launches of one step at 128^3: 2 x DFMA + DADD + DMUL thread instructions counted by ncu,
-# an ncu capture of this kernel); the kernel is FP64-ALU bound
-ASSEMBLE_FP64_FLOPS_PER_CELL = 1591.0
-# its DRAM traffic per cell (dram__bytes_read.sum + dram__bytes_write.sum, mean over the same
-# five launches at 128^3, where the kernel's arrays are well above L2), scaled to a launch
-ASSEMBLE_DRAM_BYTES_PER_CELL = 198.9
+# FP64 flops per cell of one newton_assemble launch on this workload: the work the kernel
+# executes (2 x DFMA + DADD + DMUL thread instructions counted by ncu), mean over the five
+# launches of one step at 128^3 (755-1421 per launch: one or two evaluations of the local
+# equations per cell); the kernel is FP64-ALU bound
+ASSEMBLE_FP64_FLOPS_PER_CELL = 1108.0
+# its DRAM traffic per cell (dram__bytes_read.sum + dram__bytes_write.sum), mean over the four
+# launches of one warm 256^3 step (ncu, the timed step only), scaled to a launch by the cells
+ASSEMBLE_DRAM_BYTES_PER_CELL = 241.8
 # FP64 flops per cell of the advection kernel with rho_b (three face Courant numbers and three
 # donor-cell updates of three densities per axis: 3 x (6 + 3 x 4)), counted from the source
 ADVECT_FP64_FLOPS_PER_CELL = 54.0
@@ -434,8 +435,8 @@ def bench_line(args, res, world, peaks):
             roof = {"kernel": dom_name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3,
                     "unit": "TFLOP/s", "frac": ach / (FP64_PEAK_GFLOPS / 1e3),
                     "traffic": ASSEMBLE_DRAM_BYTES_PER_CELL * cells,
-                    "traffic_source": "ncu DRAM bytes per cell of this kernel at 128^3 times the cells "
-                                      "of one launch",
+                    "traffic_source": "ncu DRAM bytes per cell of this kernel in one warm 256^3 step times "
+                                      "the cells of one launch",
                     "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (own probe: 1.19 TFLOP/s)",
                     "flops_per_cell": ASSEMBLE_FP64_FLOPS_PER_CELL, "share_of_step": dom["ms"] / res["ms"]}
         else:
