@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--no-advect", action="store_true", help="skip the advection pre-step measurement")
+    p.add_argument("--helium", action="store_true",
+                   help="time the hydrogen + helium version of the field (Y = 0.24); no CPU baseline")
     return p.parse_args()
 
 
@@ -81,6 +83,10 @@ ASSEMBLE_FP64_FLOPS_PER_CELL = 1108.0
 # its DRAM traffic per cell (dram__bytes_read.sum + dram__bytes_write.sum), mean over the four
 # launches of one warm 256^3 step (ncu, the timed step only), scaled to a launch by the cells
 ASSEMBLE_DRAM_BYTES_PER_CELL = 241.8
+# the same two figures for the hydrogen + helium kernel (--helium): mean over the four launches
+# of one step of the 128^3 field with helium (ncu), 2347-5469 flops per launch
+ASSEMBLE_HE_FP64_FLOPS_PER_CELL = 4227.0
+ASSEMBLE_HE_DRAM_BYTES_PER_CELL = 221.0
 # FP64 flops per cell of the advection kernel with rho_b (three face Courant numbers and three
 # donor-cell updates of three densities per axis: 3 x (6 + 3 x 4)), counted from the source
 ADVECT_FP64_FLOPS_PER_CELL = 54.0
@@ -157,7 +163,8 @@ class ClockSampler:
 def _final_state(s):
     """(E, x_HI, T) of a solver's current state on the host (CGS E, temperature in K)."""
     from paper_0908_2654_gb300.units import temperature
-    ec, nHI, E = s.state_cgs()
+    st = s.state_cgs()
+    nHI, E = st[1], st[-1]
     u = s.units
     rho = s.rho.cpu().numpy() * u.u_d
     v = tuple(x.cpu().numpy() * u.u_v for x in s.v)
@@ -213,6 +220,9 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     n = args.size
     w = workload(n)
+    if args.helium:
+        import workloads as W
+        w = W.with_helium(w)
     cells = n**3
 
     def barrier():
@@ -417,6 +427,7 @@ def bench_line(args, res, world, peaks):
     profile, kernel table, launch count)."""
     prof = res["prof"] or {}
     dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
+    helium = getattr(args, "helium", False)
     roof = None
     cells = args.size**3
     hbm_peak = (peaks or {}).get("hbm_gbs", 6800.0)
@@ -431,14 +442,17 @@ def bench_line(args, res, world, peaks):
     if dom is not None:
         if dom_name == "newton_assemble":
             ms = dom["ms"] / dom["launches"]
-            ach = ASSEMBLE_FP64_FLOPS_PER_CELL * cells / (ms * 1e-3) / 1e12
+            fpc = ASSEMBLE_HE_FP64_FLOPS_PER_CELL if helium else ASSEMBLE_FP64_FLOPS_PER_CELL
+            bpc = ASSEMBLE_HE_DRAM_BYTES_PER_CELL if helium else ASSEMBLE_DRAM_BYTES_PER_CELL
+            ach = fpc * cells / (ms * 1e-3) / 1e12
             roof = {"kernel": dom_name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3,
                     "unit": "TFLOP/s", "frac": ach / (FP64_PEAK_GFLOPS / 1e3),
-                    "traffic": ASSEMBLE_DRAM_BYTES_PER_CELL * cells,
-                    "traffic_source": "ncu DRAM bytes per cell of this kernel in one warm 256^3 step times "
-                                      "the cells of one launch",
+                    "traffic": bpc * cells,
+                    "traffic_source": ("ncu DRAM bytes per cell of this kernel at 128^3" if helium else
+                                       "ncu DRAM bytes per cell of this kernel in one warm 256^3 step") +
+                                      " times the cells of one launch",
                     "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (own probe: 1.19 TFLOP/s)",
-                    "flops_per_cell": ASSEMBLE_FP64_FLOPS_PER_CELL, "share_of_step": dom["ms"] / res["ms"]}
+                    "flops_per_cell": fpc, "share_of_step": dom["ms"] / res["ms"]}
         else:
             roof = hbm_roof(dom_name, dom)
     # the smoother over all levels, and its fine-level passes alone (the coarse levels are a few
@@ -467,7 +481,7 @@ def bench_line(args, res, world, peaks):
                    "share": v["ms"] / res["ms"]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
     launches = sum(x["kernel_launches"] for x in res["stats"]) + len(res["stats"])
     w_desc = (f"reionization-like field {args.size}^3, {workload_sources(args.size)} sources, z=9, dt=1 Myr, "
-              "theta=1")
+              "theta=1" + (", hydrogen + helium (Y = 0.24)" if helium else ""))
     config = {"workload": w_desc, "grid": args.size, "precision": "mixed (FP32 multigrid in FP64 Newton/CG)",
               "newton_tol": args.newton_tol, "lin_rtol": args.lin_rtol, "parallelism": f"replicas x{world}",
               "l2": l2_note(args.size)}
@@ -523,7 +537,7 @@ def main():
     if rank != 0:
         return
     line = bench_line(args, res, world, load_peaks())
-    if not args.no_cpu and world == 1:
+    if not args.no_cpu and not args.helium and world == 1:
         line["cpu_baseline"] = cpu_baseline(res["w"], args.newton_tol)
     print(json.dumps(line))
 

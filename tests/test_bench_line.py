@@ -63,6 +63,15 @@ def test_config_describes_the_workload_at_each_size():
         assert bench.workload_sources(n) == nsrc
 
 
+def test_helium_option_uses_the_helium_kernel_figures():
+    args = argparse.Namespace(size=128, steps=2, warmup=3, newton_tol=1e-6, lin_rtol=1e-3, helium=True)
+    line = bench.bench_line(args, _res(), 1, {"hbm_gbs": 6797.2})
+    assert "hydrogen + helium" in line["config"]["workload"]
+    roof = line["roofline"]
+    assert roof["flops_per_cell"] == bench.ASSEMBLE_HE_FP64_FLOPS_PER_CELL
+    assert roof["traffic"] == pytest.approx(bench.ASSEMBLE_HE_DRAM_BYTES_PER_CELL * 128**3)
+
+
 def test_reference_arm_line(capsys):
     """bench.py --impl reference: the oracle on host cores prints one JSON line with the
     contract's keys, a cpu_baseline describing the run and a zero-copy e2e."""
