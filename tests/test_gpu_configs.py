@@ -1,10 +1,12 @@
 """The five workload configurations at their stated sizes, checked through properties that hold
 at any size (the oracle cannot run them whole):
 
-* static Stromgren sphere, FP64, 128^3 (reflecting lower and outflow upper faces): the
-  configuration's steps of 0.01 t_rec, each halved when Newton fails at it (the paper runs
-  the problem under its time-step control), to t_rec; the I-front radius against
-  R_s (1 - e^{-t/t_rec})^{1/3}.  The 256^3 run to 2 t_rec is opt-in (RT_LONG_TESTS=1);
+* static Stromgren sphere, FP64 (reflecting lower and outflow upper faces): the configuration's
+  steps of 0.01 t_rec, each halved when Newton fails at it (the paper runs the problem under its
+  time-step control); the I-front radius against R_s (1 - e^{-t/t_rec})^{1/3} at 128^3 to
+  t_rec / 2 and at 256^3 to t_rec / 5.  Past about 0.6 t_rec the preconditioned CG needs a few
+  hundred iterations per Newton step at 128^3 and Newton needs many step halvings; the runs to
+  t_rec (128^3) and 2 t_rec (256^3) are opt-in (RT_LONG_TESTS=1);
 * cosmological Stromgren sphere, FP64, 128^3, flat LCDM from z = 10 to z = 4 with the adaptive
   controller: the front against the oracle's integration of the expanding-universe I-front
   equation;
@@ -32,7 +34,7 @@ from oracle import driver  # noqa: E402
 from oracle import model as M  # noqa: E402
 
 
-# the 256^3 Stromgren run takes many minutes: opt in with RT_LONG_TESTS=1
+# the Stromgren runs to one and two recombination times take many minutes: opt in with RT_LONG_TESTS=1
 LONG = pytest.mark.skipif(os.environ.get("RT_LONG_TESTS") != "1",
                           reason="long validation run; set RT_LONG_TESTS=1")
 
@@ -47,10 +49,12 @@ def _neff(w, s):
     return w["ndot_total"] * g["eps_src"] * g["sigma_G"] / g["sigma_E"]
 
 
-def _static_stromgren_run(n, t_ends):
-    """Steps of 0.01 t_rec (halved where Newton fails, then back), front errors at t_ends [t_rec]."""
+def _static_stromgren_run(n, t_ends, max_newton=15, max_lin=500):
+    """Steps of 0.01 t_rec (halved where Newton fails, then back), front errors at t_ends [t_rec].
+    A Newton solve that cannot converge in 15 iterations with at most 500 CG iterations each is
+    retried at half the step rather than pushed further."""
     w = W.stromgren_static(n=n, nsteps=200)
-    s = _solver(w, precision="fp64", newton_tol=1e-8, lin_rtol=1e-6, max_newton=40, max_lin=2000)
+    s = _solver(w, precision="fp64", newton_tol=1e-8, lin_rtol=1e-6, max_newton=max_newton, max_lin=max_lin)
     neff = _neff(w, s)
     t_rec = w["t_rec"]
     errs, steps = [], []
@@ -64,18 +68,31 @@ def _static_stromgren_run(n, t_ends):
     return np.array(errs), steps
 
 
-def test_static_stromgren_128_configuration_steps():
-    """The 128^3 configuration to t_rec in its 0.01 t_rec steps (100 of them unless Newton needs
-    a step halved): the front within 8 % of the closed form from 0.25 t_rec on (the diffuse
-    FLD front lags the sharp closed-form one most while it is young)."""
-    errs, steps = _static_stromgren_run(128, (0.25, 0.5, 1.0))
+def test_static_stromgren_128_to_half_a_recombination_time():
+    """128^3 in the configuration's 0.01 t_rec steps to t_rec / 2: the front within 8 % of the
+    closed form at 0.25 and 0.5 t_rec (the diffuse FLD front lags the sharp closed-form one most
+    while it is young; measured 5.7 % and 4.0 %)."""
+    errs, steps = _static_stromgren_run(128, (0.25, 0.5))
     assert np.all(np.abs(errs) < 0.08), (errs, steps)
     assert steps[0] >= 25
 
 
+def test_static_stromgren_256_to_a_fifth_of_a_recombination_time():
+    """256^3 in 0.01 t_rec steps to t_rec / 5: the front within 8 % of the closed form."""
+    errs, steps = _static_stromgren_run(256, (0.2,))
+    assert np.all(np.abs(errs) < 0.08), (errs, steps)
+    assert steps[0] >= 20
+
+
+@LONG
+def test_static_stromgren_128_to_one_recombination_time():
+    errs, steps = _static_stromgren_run(128, (0.25, 0.5, 1.0), max_newton=40, max_lin=2000)
+    assert np.all(np.abs(errs) < 0.08), (errs, steps)
+
+
 @LONG
 def test_static_stromgren_256_to_two_recombination_times():
-    errs, steps = _static_stromgren_run(256, (0.25, 0.5, 1.0, 1.5, 2.0))
+    errs, steps = _static_stromgren_run(256, (0.25, 0.5, 1.0, 1.5, 2.0), max_newton=40, max_lin=2000)
     assert np.all(np.abs(errs) < 0.08), (errs, steps)
 
 
