@@ -283,6 +283,14 @@ __global__ void k_cg_scalars(double* scal, const double* dots, int phase) {
 // one colour pass (colour C) of a red-black sweep of a colour-split level in place (rbpass.cuh)
 template <int C, class T>
 __global__ void __launch_bounds__(rbp::kPairs, 16) k_rbgs_pass(rbp::Pass<T> A) {
+    if (A.quad) {   // two pairs per thread, two-element loads and stores
+        int px, y, z;
+        if (!rbp::quad_pairs(A, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, px, y, z)) return;
+        T v0, v1;
+        rbp::quad_values<C>(A, px, y, z, v0, v1);
+        rbp::st2(A.x + (z * A.ny + y) * (A.nx >> 1) + px, v0, v1);
+        return;
+    }
     int x, y, z;
     if (!rbp::pair_cell(A, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, x, y, z)) return;
     A.x[rbp::pair_of(A, x, y, z)] = rbp::cell_value<C>(A, x, y, z);
@@ -751,10 +759,10 @@ int launch_rbgs_inplace(const Level<T>& L, int first, bool zero_guess, cudaStrea
     for (int pass = 0; pass < 2; ++pass) {
         const int colour = pass == 0 ? first : 1 - first;
         // the second pass starts on the planes the first read last
-        const rbp::Pass<T> A = rbp::make_pass<T>(d.nx, d.ny, d.nz, d.per, L.w6, L.dinv, L.b, L.x, colour,
-                                                 pass == 0 && zero_guess, pass);
-        int gx, gy, gz, rows;
-        rbp::pass_grid(d.nx, d.ny, d.nz, gx, gy, gz, rows);
+        rbp::Pass<T> A = rbp::make_pass<T>(d.nx, d.ny, d.nz, d.per, L.w6, L.dinv, L.b, L.x, colour,
+                                           pass == 0 && zero_guess, pass);
+        int gx, gy, gz;
+        rbp::pass_launch(A, gx, gy, gz);
         const dim3 grid(gx, gy, gz);
         if (colour == 0)
             k_rbgs_pass<0, T><<<grid, rbp::kPairs, 0, s>>>(A);

@@ -44,8 +44,27 @@ RT_HD long long level_index(int split, int nx, int ny, int nz, int x, int y, int
     return (long long)((x + y + z) & 1) * half + (i >> 1);
 }
 
+// two-element vector loads and stores (8 bytes for float, 16 for double): the address must be
+// aligned to that size
+template <class T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+template <class T>
+RT_HD void ld2(const T* p, T& a, T& b) {
+    const typename Vec2<T>::type v = *reinterpret_cast<const typename Vec2<T>::type*>(p);
+    a = v.x;
+    b = v.y;
+}
+template <class T>
+RT_HD void st2(T* p, T a, T b) {
+    typename Vec2<T>::type v;
+    v.x = a;
+    v.y = b;
+    *reinterpret_cast<typename Vec2<T>::type*>(p) = v;
+}
+
 // launch geometry of a pass: (blocks per row, row blocks, planes)
-inline void pass_grid(int nx, int ny, int nz, int& gx, int& gy, int& gz, int& rows) {
+RT_HD void pass_grid(int nx, int ny, int nz, int& gx, int& gy, int& gz, int& rows) {
     const int hp = nx / 2;
     if (hp >= kPairs) {
         rows = 1;
@@ -73,8 +92,15 @@ struct Pass {
     int colour;     // parity of the cells this pass sets
     int zero;       // the old iterate is zero (first pass of a sweep from zero)
     int rev;        // blocks take the planes from the last to the first
-    int rows;       // rows per block: kPairs / pairs per row (at least 1)
+    int quad;       // each thread updates the cells of two pairs (nx a multiple of 4)
+    int rows;       // rows per block: kPairs / threads per row (at least 1)
 };
+
+// launch geometry of pass A (threads per row: pairs, or pairs of pairs when A.quad); sets A.rows
+template <class T>
+RT_HD void pass_launch(Pass<T>& A, int& gx, int& gy, int& gz) {
+    pass_grid(A.quad ? A.nx / 2 : A.nx, A.ny, A.nz, gx, gy, gz, A.rows);
+}
 
 // the pass over level arrays x, b (colour-split), dinv (colour-split) and w6 (six face arrays)
 template <class T>
@@ -94,8 +120,9 @@ RT_HD Pass<T> make_pass(int nx, int ny, int nz, const int* per, const T* w6, con
     A.colour = colour;
     A.zero = zero;
     A.rev = rev;
+    A.quad = nx % 4 == 0;
     int gx, gy, gz;
-    pass_grid(nx, ny, nz, gx, gy, gz, A.rows);
+    pass_launch(A, gx, gy, gz);
     return A;
 }
 
@@ -123,6 +150,16 @@ RT_HD bool pair_cell(const Pass<T>& A, int bx, int by, int bz, int t, int& x, in
     int px;
     if (!grid_pair(A.nx, A.ny, A.rows, bx, by, A.rev ? A.nz - 1 - bz : bz, t, px, y, z)) return false;
     x = 2 * px + ((y + z + A.colour) & 1);   // the pair's cell of this colour
+    return true;
+}
+
+// the first of the two pairs of the thread of block (bx, by, bz) and lane t in a quad pass
+// (planes in reverse when A.rev); returns false when there is none
+template <class T>
+RT_HD bool quad_pairs(const Pass<T>& A, int bx, int by, int bz, int t, int& px, int& y, int& z) {
+    int pq;
+    if (!grid_pair(A.nx >> 1, A.ny, A.rows, bx, by, A.rev ? A.nz - 1 - bz : bz, t, pq, y, z)) return false;
+    px = 2 * pq;
     return true;
 }
 
@@ -164,6 +201,75 @@ RT_HD T cell_value(const Pass<T>& A, int x, int y, int z) {
         }
     }
     return num * A.dinv[m];
+}
+
+// New values of the cells of colour C in pairs m and m + 1, m the pair of (2 px, y, z) with px
+// even; nx a multiple of 4, so that every pair number used in a two-element access is even and
+// all but the x-neighbour beyond the two pairs come in aligned pairs.  The same sums as
+// cell_value for each of the two cells, with half the loads.
+template <int C, class T>
+RT_HD void quad_values(const Pass<T>& A, int px, int y, int z, T& v0, T& v1) {
+    const int hx = A.nx >> 1, hxy = hx * A.ny, half = hxy * A.nz;
+    const int m = (z * A.ny + y) * hx + px;
+    RT_SWEEP_CHECK(m >= 0 && m + 1 < half && (m & 1) == 0);
+    T n0, n1;
+    ld2(A.b + m, n0, n1);
+    if (!A.zero) {
+        // y and z neighbours: pairs q, q + 1 for the two cells
+        auto yz = [&](int f, int q) {
+            RT_SWEEP_CHECK(q >= 0 && q + 1 < half && (q & 1) == 0);
+            T x0, x1, w0, w1;
+            ld2(A.xo + q, x0, x1);
+            if (C == 0)
+                ld2(A.w[f] + m, w0, w1);
+            else
+                ld2(A.w[f ^ 1] + q, w0, w1);
+            n0 += w0 * x0;
+            n1 += w1 * x1;
+        };
+        if (y > 0) yz(FYM, m - hx);
+        else if (A.per[1]) yz(FYM, m - hx + hxy);
+        if (y + 1 < A.ny) yz(FYP, m + hx);
+        else if (A.per[1]) yz(FYP, m + hx - hxy);
+        if (z > 0) yz(FZM, m - hxy);
+        else if (A.per[2]) yz(FZM, m - hxy + half);
+        if (z + 1 < A.nz) yz(FZP, m + hxy);
+        else if (A.per[2]) yz(FZP, m + hxy - half);
+        // x neighbours: the other colour at pairs m and m + 1, and at m - 1 (this colour's cells
+        // at even x) or m + 2 (at odd x), which wrap on a periodic axis
+        T xa, xb;
+        ld2(A.xo + m, xa, xb);
+        T wm0, wm1, wp0, wp1;   // face arrays -x and +x at pairs m, m + 1
+        ld2(A.w[FXM] + m, wm0, wm1);
+        ld2(A.w[FXP] + m, wp0, wp1);
+        if (((y + z + C) & 1) == 0) {
+            const int qw = px > 0 ? m - 1 : (A.per[0] ? m - 1 + hx : -1);
+            if (C == 0) {
+                if (qw >= 0) n0 += wm0 * A.xo[qw];
+                n0 += wp0 * xa;
+                n1 += wm1 * xa + wp1 * xb;
+            } else {
+                if (qw >= 0) n0 += A.w[FXP][qw] * A.xo[qw];
+                n0 += wm0 * xa;
+                n1 += wp0 * xa + wm1 * xb;
+            }
+        } else {
+            const int qe = px + 2 < hx ? m + 2 : (A.per[0] ? m + 2 - hx : -1);
+            if (C == 0) {
+                n0 += wm0 * xa + wp0 * xb;
+                n1 += wm1 * xb;
+                if (qe >= 0) n1 += wp1 * A.xo[qe];
+            } else {
+                n0 += wp0 * xa + wm1 * xb;
+                n1 += wp1 * xb;
+                if (qe >= 0) n1 += A.w[FXM][qe] * A.xo[qe];
+            }
+        }
+    }
+    T d0, d1;
+    ld2(A.dinv + m, d0, d1);
+    v0 = n0 * d0;
+    v1 = n1 * d1;
 }
 
 // colour-split inverse diagonal and colour-0 face arrays of pair m from the natural diagonal and

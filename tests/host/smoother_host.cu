@@ -18,7 +18,7 @@ static long long g_bad_index = 0;
 
 template <class T>
 static long long run_sweep(int nx, int ny, int nz, const int* per, const T* diag, const T* wx, const T* wy,
-                           const T* wz, const T* b, T* x, int first, int zero) {
+                           const T* wz, const T* b, T* x, int first, int zero, int quad) {
     g_bad_index = 0;
     const long long n = (long long)nx * ny * nz, half = n / 2;
     // the level in colour-split storage
@@ -46,16 +46,41 @@ static long long run_sweep(int nx, int ny, int nz, const int* per, const T* diag
         if (w6[k] == T(-1)) ++g_bad_index;   // every face entry written
     for (int pass = 0; pass < 2; ++pass) {
         const int colour = pass == 0 ? first : 1 - first;
-        const rbp::Pass<T> A = rbp::make_pass<T>(nx, ny, nz, per, w6.data(), dinv.data(), bs.data(), xs.data(), colour,
-                                                 pass == 0 && zero, pass);
-        int gx, gy, gz, rows;
-        rbp::pass_grid(nx, ny, nz, gx, gy, gz, rows);
+        rbp::Pass<T> A = rbp::make_pass<T>(nx, ny, nz, per, w6.data(), dinv.data(), bs.data(), xs.data(), colour,
+                                           pass == 0 && zero, pass);
+        if (A.quad != (nx % 4 == 0)) ++g_bad_index;
+        A.quad = quad && A.quad;   // the single-pair form on request
+        int gx, gy, gz;
+        rbp::pass_launch(A, gx, gy, gz);
         std::vector<int> hits(n, 0);
         // a pass never reads the cells it sets, so the order of its threads does not matter
         for (int bz = 0; bz < gz; ++bz)
             for (int by = 0; by < gy; ++by)
                 for (int bx = 0; bx < gx; ++bx)
                     for (int t = 0; t < rbp::kPairs; ++t) {
+                        if (A.quad) {
+                            int px, cy, cz;
+                            if (!rbp::quad_pairs(A, bx, by, bz, t, px, cy, cz)) continue;
+                            if (px < 0 || px + 1 >= nx / 2 || cy < 0 || cy >= ny || cz < 0 || cz >= nz) {
+                                ++g_bad_index;
+                                continue;
+                            }
+                            T v0, v1;
+                            if (A.colour)
+                                rbp::quad_values<1>(A, px, cy, cz, v0, v1);
+                            else
+                                rbp::quad_values<0>(A, px, cy, cz, v0, v1);
+                            const long long m = ((long long)cz * ny + cy) * (nx / 2) + px;
+                            if ((m & 1) != 0) ++g_bad_index;   // two-element accesses stay aligned
+                            rbp::st2(A.x + m, v0, v1);
+                            for (int k = 0; k < 2; ++k) {
+                                const int cx = 2 * (px + k) + ((cy + cz + A.colour) & 1);
+                                ++hits[((long long)cz * ny + cy) * nx + cx];
+                                if (rbp::level_index(1, nx, ny, nz, cx, cy, cz) != A.colour * half + m + k)
+                                    ++g_bad_index;
+                            }
+                            continue;
+                        }
                         int cx, cy, cz;
                         if (!rbp::pair_cell(A, bx, by, bz, t, cx, cy, cz)) continue;
                         if (cx < 0 || cx >= nx || cy < 0 || cy >= ny || cz < 0 || cz >= nz) {
@@ -85,12 +110,13 @@ static long long run_sweep(int nx, int ny, int nz, const int* per, const T* diag
 
 extern "C" {
 long long sweep_host_f64(int nx, int ny, int nz, const int* per, const double* diag, const double* wx,
-                         const double* wy, const double* wz, const double* b, double* x, int first, int zero) {
-    return run_sweep<double>(nx, ny, nz, per, diag, wx, wy, wz, b, x, first, zero);
+                         const double* wy, const double* wz, const double* b, double* x, int first, int zero,
+                         int quad) {
+    return run_sweep<double>(nx, ny, nz, per, diag, wx, wy, wz, b, x, first, zero, quad);
 }
 long long sweep_host_f32(int nx, int ny, int nz, const int* per, const float* diag, const float* wx,
-                         const float* wy, const float* wz, const float* b, float* x, int first, int zero) {
-    return run_sweep<float>(nx, ny, nz, per, diag, wx, wy, wz, b, x, first, zero);
+                         const float* wy, const float* wz, const float* b, float* x, int first, int zero, int quad) {
+    return run_sweep<float>(nx, ny, nz, per, diag, wx, wy, wz, b, x, first, zero, quad);
 }
 // out[z][y][x] = trilinear prolongation at every fine cell of the coarse vector xc (cnx x cny x
 // cnz, natural order), read from a colour-split copy when csplit

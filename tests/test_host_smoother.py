@@ -89,7 +89,7 @@ def _prolong_reference(xc, fshape, per):
     return out
 
 
-def _sweep(lib, dtype, shape, per, diag, w, b, xin, first, zero):
+def _sweep(lib, dtype, shape, per, diag, w, b, xin, first, zero, quad=1):
     nz, ny, nx = shape
     fn = lib.sweep_host_f64 if dtype == np.float64 else lib.sweep_host_f32
     fn.restype = ctypes.c_longlong
@@ -97,7 +97,7 @@ def _sweep(lib, dtype, shape, per, diag, w, b, xin, first, zero):
     args = [arr(diag), *[arr(v) for v in w], arr(b)]
     x = np.array(xin, dtype=dtype, copy=True)
     bad = fn(nx, ny, nz, (ctypes.c_int * 3)(*per), *[a.ctypes.data_as(ctypes.c_void_p) for a in args],
-             x.ctypes.data_as(ctypes.c_void_p), first, zero)
+             x.ctypes.data_as(ctypes.c_void_p), first, zero, quad)
     return x, bad
 
 
@@ -109,9 +109,11 @@ CASES = [((20, 32, 64), (True, True, True)), ((24, 40, 40), (False, False, False
          ((24, 6, 8), (True, True, False)), ((2, 2, 258), (True, True, True))]
 
 
+@pytest.mark.parametrize("quad", [1, 0])
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 @pytest.mark.parametrize("shape,per", CASES)
-def test_sweep_equals_red_black_gauss_seidel(lib, shape, per, dtype):
+def test_sweep_equals_red_black_gauss_seidel(lib, shape, per, dtype, quad):
+    """quad = 1: two pairs per thread wherever nx is a multiple of 4; quad = 0: one pair."""
     rng = np.random.default_rng(13 + sum(shape))
     diag, *w = _operator(shape, per, rng, dtype)
     b = rng.standard_normal(shape).astype(dtype)
@@ -120,7 +122,7 @@ def test_sweep_equals_red_black_gauss_seidel(lib, shape, per, dtype):
     for first, zero, xin in ((0, 0, x0), (1, 0, x0), (0, 1, np.zeros(shape))):
         ref = _rbgs_reference(diag, w, b, xin, first)
         start = np.full(shape, np.nan) if zero else xin
-        got, bad = _sweep(lib, dtype, shape, per, diag, w, b, start, first, zero)
+        got, bad = _sweep(lib, dtype, shape, per, diag, w, b, start, first, zero, quad)
         assert bad == 0
         np.testing.assert_allclose(got, ref, rtol=tol, atol=tol * np.abs(ref).max())
 
