@@ -19,6 +19,7 @@
 #include "cellgrid.cuh"
 #include "kernels.cuh"
 #include "rbpass.cuh"
+#include "fpbits.cuh"
 
 namespace {
 
@@ -196,28 +197,30 @@ __global__ void k_cast_d2f(long long n, const double* __restrict__ a, float* __r
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         b[i] = (float)a[i];
 }
-// 2^-e with 2^e >= amax: an exact power-of-two scale
-__device__ __forceinline__ double pow2_scale(double amax, bool inverse) {
-    int e = 0;
-    if (amax > 0.0 && isfinite(amax)) frexp(amax, &e);   // amax < 2^e
-    return ldexp(1.0, inverse ? e : -e);
-}
-// level-0 vectors in the multigrid's storage order, scaled by 2^-e (2^e >= *amax) on the way in
-// and by 2^e on the way out (no scaling when amax is null).  Natural order: thread per cell.
+// Level-0 vectors in the multigrid's storage order, as r 2^-e on the way in and x 2^e on the way
+// out (2^e >= *amax; e = 0 when amax is null).  Between FP64 and FP32 the scaled conversion works
+// on the bit patterns (fpbits.cuh); FP64 to FP64 is a permutation.
+__device__ __forceinline__ int scale_exponent(const double* amax) { return amax ? fpbits::pow2_exponent(*amax) : 0; }
+__device__ __forceinline__ float cvt_in(double v, int e, float*) { return fpbits::to_float_scaled(v, e); }
+__device__ __forceinline__ double cvt_in(double v, int, double*) { return v; }
+__device__ __forceinline__ double cvt_out(float v, int e) { return fpbits::from_float_scaled(v, e); }
+__device__ __forceinline__ double cvt_out(double v, int) { return v; }
+
+// natural order: thread per cell
 template <class Tin, class Tout>
 __global__ void k_to_level(Dims d, const Tin* __restrict__ a, Tout* __restrict__ out, const double* __restrict__ amax) {
-    const double sc = amax ? pow2_scale(*amax, false) : 1.0;
+    const int e = scale_exponent(amax);
     const long long n = d.n();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = (Tout)((double)a[i] * sc);
+        out[i] = cvt_in(a[i], e, (Tout*)nullptr);
 }
 template <class Tin, class Tout>
 __global__ void k_from_level(Dims d, const Tin* __restrict__ a, Tout* __restrict__ out,
                              const double* __restrict__ amax) {
-    const double sc = amax ? pow2_scale(*amax, true) : 1.0;
+    const int e = scale_exponent(amax);
     const long long n = d.n();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = (Tout)((double)a[i] * sc);
+        out[i] = cvt_out(a[i], e);
 }
 // Colour-split order: thread per x-pair (one 16-byte load or store of the FP64 pair, one element
 // into or out of each colour half), launched in pass_grid's shape so that no index is divided
@@ -226,26 +229,26 @@ __global__ void __launch_bounds__(rbp::kPairs) k_to_split(Dims d, int rows, cons
                                                           Tout* __restrict__ out, const double* __restrict__ amax) {
     int px, y, z;
     if (!rbp::grid_pair(d.nx, d.ny, rows, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, px, y, z)) return;
-    const double sc = amax ? pow2_scale(*amax, false) : 1.0;
+    const int e = scale_exponent(amax);
     const long long hx = d.nx >> 1, half = hx * d.ny * d.nz;
     const long long m = ((long long)z * d.ny + y) * hx + px;
     const int c0 = (y + z) & 1;   // colour of the pair's even-x cell
     const double2 v = reinterpret_cast<const double2*>(a)[m];
-    out[c0 * half + m] = (Tout)(v.x * sc);
-    out[(1 - c0) * half + m] = (Tout)(v.y * sc);
+    out[c0 * half + m] = cvt_in(v.x, e, (Tout*)nullptr);
+    out[(1 - c0) * half + m] = cvt_in(v.y, e, (Tout*)nullptr);
 }
 template <class Tin>
 __global__ void __launch_bounds__(rbp::kPairs) k_from_split(Dims d, int rows, const Tin* __restrict__ a,
                                                             double* __restrict__ out, const double* __restrict__ amax) {
     int px, y, z;
     if (!rbp::grid_pair(d.nx, d.ny, rows, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, px, y, z)) return;
-    const double sc = amax ? pow2_scale(*amax, true) : 1.0;
+    const int e = scale_exponent(amax);
     const long long hx = d.nx >> 1, half = hx * d.ny * d.nz;
     const long long m = ((long long)z * d.ny + y) * hx + px;
     const int c0 = (y + z) & 1;
     double2 v;
-    v.x = (double)a[c0 * half + m] * sc;
-    v.y = (double)a[(1 - c0) * half + m] * sc;
+    v.x = cvt_out(a[c0 * half + m], e);
+    v.y = cvt_out(a[(1 - c0) * half + m], e);
     reinterpret_cast<double2*>(out)[m] = v;
 }
 __global__ void k_cast_f2d(long long n, const float* __restrict__ a, double* __restrict__ b) {
