@@ -170,15 +170,10 @@ int launch_cg_update_xr(long long n, const double* scal, double* x, double* r, c
                         const double* w, double* partials, cudaStream_t s);
 int launch_dot2(long long n, const double* z, const double* r, const double* q, double* partials, cudaStream_t s);
 void launch_p_update(long long n, const double* scal, const double* z, double* p, cudaStream_t s);
-void launch_cast_d2f(long long n, const double* a, float* b, cudaStream_t s);
-// b = a * 2^-k and back, with 2^k >= *amax (keeps an FP64 vector inside the FP32 range)
-void launch_cast_d2f_scaled(long long n, const double* a, float* b, const double* amax, cudaStream_t s);
-void launch_cast_f2d_scaled(long long n, const float* a, double* b, const double* amax, cudaStream_t s);
 // multigrid operator diagonal: max(diag, sum of the 6 face couplings), i.e. sigma = max(sigma, 0)
 template <class T>
 void launch_mg_diag(const Dims& D, const double* diag, const double* wx, const double* wy, const double* wz, T* out,
                     cudaStream_t s);
-void launch_cast_f2d(long long n, const float* a, double* b, cudaStream_t s);
 void launch_copy(long long n, const double* a, double* b, cudaStream_t s);
 void launch_add(long long n, const double* a, double* b, cudaStream_t s);   // b += a
 // scalar bookkeeping on the device: scal[] holds alpha, beta and the dot products

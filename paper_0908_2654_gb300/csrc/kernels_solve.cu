@@ -193,10 +193,6 @@ __global__ void k_mg_diag(Dims d, const double* __restrict__ diag, const double*
     }
 }
 
-__global__ void k_cast_d2f(long long n, const double* __restrict__ a, float* __restrict__ b) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        b[i] = (float)a[i];
-}
 // Level-0 vectors in the multigrid's storage order, as r 2^-e on the way in and x 2^e on the way
 // out (2^e >= *amax; e = 0 when amax is null).  Between FP64 and FP32 the scaled conversion works
 // on the bit patterns (fpbits.cuh); FP64 to FP64 is a permutation.
@@ -250,10 +246,6 @@ __global__ void __launch_bounds__(rbp::kPairs) k_from_split(Dims d, int rows, co
     v.x = cvt_out(a[c0 * half + m], e);
     v.y = cvt_out(a[(1 - c0) * half + m], e);
     reinterpret_cast<double2*>(out)[m] = v;
-}
-__global__ void k_cast_f2d(long long n, const float* __restrict__ a, double* __restrict__ b) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        b[i] = (double)a[i];
 }
 __global__ void k_add(long long n, const double* __restrict__ a, double* __restrict__ b) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -698,12 +690,6 @@ int launch_dot2(long long n, const double* z, const double* r, const double* q, 
 }
 void launch_p_update(long long n, const double* scal, const double* z, double* p, cudaStream_t s) {
     k_p_update<<<grid_for(n), kBlock, 0, s>>>(n, scal, z, p);
-}
-void launch_cast_d2f(long long n, const double* a, float* b, cudaStream_t s) {
-    k_cast_d2f<<<grid_for(n), kBlock, 0, s>>>(n, a, b);
-}
-void launch_cast_f2d(long long n, const float* a, double* b, cudaStream_t s) {
-    k_cast_f2d<<<grid_for(n), kBlock, 0, s>>>(n, a, b);
 }
 template <class Tin, class Tout>
 void launch_to_level(const Dims& d, int split, const Tin* a, Tout* out, const double* amax, cudaStream_t s) {
