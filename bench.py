@@ -77,16 +77,16 @@ def l2_note(n):
 
 # FP64 flops per cell of one newton_assemble launch on this workload: the work the kernel
 # executes (2 x DFMA + DADD + DMUL thread instructions counted by ncu), mean over the five
-# launches of one step at 128^3 (755-1421 per launch: one or two evaluations of the local
+# launches of one step at 128^3 (743-1419 per launch: one or two evaluations of the local
 # equations per cell); the kernel is FP64-ALU bound
-ASSEMBLE_FP64_FLOPS_PER_CELL = 1108.0
-# its DRAM traffic per cell (dram__bytes_read.sum + dram__bytes_write.sum), mean over the four
+ASSEMBLE_FP64_FLOPS_PER_CELL = 1107.0
+# its DRAM traffic per cell (dram__bytes_read.sum + dram__bytes_write.sum), mean over the five
 # launches of one warm 256^3 step (ncu, the timed step only), scaled to a launch by the cells
-ASSEMBLE_DRAM_BYTES_PER_CELL = 241.8
+ASSEMBLE_DRAM_BYTES_PER_CELL = 243.5
 # the same two figures for the hydrogen + helium kernel (--helium): mean over the four launches
 # of one step of the 128^3 field with helium (ncu), 2347-5469 flops per launch
 ASSEMBLE_HE_FP64_FLOPS_PER_CELL = 4227.0
-ASSEMBLE_HE_DRAM_BYTES_PER_CELL = 221.0
+ASSEMBLE_HE_DRAM_BYTES_PER_CELL = 220.1
 # FP64 flops per cell of the advection kernel with rho_b (three face Courant numbers and three
 # donor-cell updates of three densities per axis: 3 x (6 + 3 x 4)), counted from the source
 ADVECT_FP64_FLOPS_PER_CELL = 54.0
