@@ -305,8 +305,8 @@ template <class T>
 __global__ void __launch_bounds__(rbp::kPairs) k_prolong_add(Level<T> c, Level<T> f, int rows) {
     int px, y, z;
     if (!rbp::grid_pair(f.d.nx, f.d.ny, rows, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, px, y, z)) return;
-    const long long hx = f.d.nx >> 1, half = hx * f.d.ny * f.d.nz;
-    const long long m = ((long long)z * f.d.ny + y) * hx + px;
+    const int hx = f.d.nx >> 1, half = hx * f.d.ny * f.d.nz;
+    const int m = (z * f.d.ny + y) * hx + px;
     const int c0 = (y + z) & 1;   // colour of the even-x cell
     T v0, v1;
     rbp::prolong_pair(c.x, c.split, c.d.nx, c.d.ny, c.d.nz, c.d.per, px, y, z, v0, v1);
@@ -314,39 +314,24 @@ __global__ void __launch_bounds__(rbp::kPairs) k_prolong_add(Level<T> c, Level<T
     f.x[(1 - c0) * half + m] += v1;
 }
 
-// b - S x at fine cell (x, y, z) of a colour-split level (operator in natural order)
+// c.b = average over the 8 children of f.b - S f.x: thread per coarse cell, whose children are
+// fine pair X of the four fine rows (2Y + j, 2Z + k) (rbp::pair_residuals), launched in the
+// passes' shape over the coarse cells
 template <class T>
-__device__ __forceinline__ T split_residual(const Level<T>& f, int x, int y, int z) {
-    const Dims& d = f.d;
-    const long long i = ((long long)z * d.ny + y) * d.nx + x;
-    const long long sy = d.nx, sz = (long long)d.nx * d.ny;
-    auto X = [&](int a, int b, int e) { return f.x[rbp::level_index(1, d.nx, d.ny, d.nz, a, b, e)]; };
-    const T wxm = (!d.per[0] && x == 0) ? T(0) : f.wx[x > 0 ? i - 1 : i - 1 + d.nx];
-    const T wym = (!d.per[1] && y == 0) ? T(0) : f.wy[y > 0 ? i - sy : i - sy + sz];
-    const T wzm = (!d.per[2] && z == 0) ? T(0) : f.wz[z > 0 ? i - sz : i - sz + sz * d.nz];
-    const T off = f.wx[i] * X(up(x, d.nx, d.per[0]), y, z) + wxm * X(dn(x, d.nx, d.per[0]), y, z) +
-                  f.wy[i] * X(x, up(y, d.ny, d.per[1]), z) + wym * X(x, dn(y, d.ny, d.per[1]), z) +
-                  f.wz[i] * X(x, y, up(z, d.nz, d.per[2])) + wzm * X(x, y, dn(z, d.nz, d.per[2]));
-    const long long s = rbp::level_index(1, d.nx, d.ny, d.nz, x, y, z);
-    return f.b[s] - (f.diag[i] * f.x[s] - off);
-}
-
-template <class T>
-__global__ void __launch_bounds__(kBlock) k_resid_restrict(Level<T> f, Level<T> c) {
-    const Dims cd = c.d;
-    const long long nc = cd.n();
-    for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < nc; I += (long long)gridDim.x * blockDim.x) {
-        int X, Y, Z;
-        cell_coords(I, cd.nx, cd.ny, X, Y, Z);
-        T sum = T(0);
+__global__ void __launch_bounds__(rbp::kPairs) k_resid_restrict(Level<T> f, Level<T> c, int rows) {
+    int X, Y, Z;
+    if (!rbp::grid_pair(2 * c.d.nx, c.d.ny, rows, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, X, Y, Z)) return;
+    T sum = T(0);
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 2; ++k)
 #pragma unroll
-            for (int j = 0; j < 2; ++j)
-#pragma unroll
-                for (int l = 0; l < 2; ++l) sum += split_residual(f, 2 * X + l, 2 * Y + j, 2 * Z + k);
-        c.b[rbp::level_index(c.split, cd.nx, cd.ny, cd.nz, X, Y, Z)] = sum * T(0.125);
-    }
+        for (int j = 0; j < 2; ++j) {
+            T rE, rO;
+            rbp::pair_residuals(f.d.nx, f.d.ny, f.d.nz, f.d.per, f.diag, f.wx, f.wy, f.wz, f.b, f.x, X, 2 * Y + j,
+                                2 * Z + k, rE, rO);
+            sum += rE + rO;
+        }
+    c.b[rbp::level_index(c.split, c.d.nx, c.d.ny, c.d.nz, X, Y, Z)] = sum * T(0.125);
 }
 
 template <class T>
@@ -770,7 +755,9 @@ void launch_prolong_add(const Level<T>& c, const Level<T>& f, cudaStream_t s) {
 
 template <class T>
 void launch_resid_restrict(const Level<T>& f, const Level<T>& c, cudaStream_t s) {
-    k_resid_restrict<T><<<grid_for(c.d.n()), kBlock, 0, s>>>(f, c);
+    int gx, gy, gz, rows;
+    rbp::pass_grid(2 * c.d.nx, c.d.ny, c.d.nz, gx, gy, gz, rows);
+    k_resid_restrict<T><<<dim3(gx, gy, gz), rbp::kPairs, 0, s>>>(f, c, rows);
 }
 template <class T>
 size_t tail_smem_bytes(const Dims& d) {

@@ -417,19 +417,68 @@ RT_HD void prolong_pair(const T* xc, int csplit, int cnx, int cny, int cnz, cons
     const int Xm = other(px, 0, cnx, per[0]), Xp = other(px, 1, cnx, per[0]);
     const int Y2 = other(Y, y & 1, cny, per[1]);
     const int Z2 = other(Z, z & 1, cnz, per[2]);
-    auto C = [&](int a, int b, int e) {
-        const long long j = level_index(csplit, cnx, cny, cnz, a, b, e);
-        RT_SWEEP_CHECK(j >= 0 && j < (long long)cnx * cny * cnz);
+    // the four coarse rows (Y or Y2, Z or Z2): row start and the parity of Y + Z; a coarse level
+    // holds at most 2^30 cells, so the indices are 32-bit
+    const int halfc = csplit ? cnx * cny * cnz / 2 : 0;
+    const int r00 = (Z * cny + Y) * cnx, r10 = (Z * cny + Y2) * cnx;
+    const int r01 = (Z2 * cny + Y) * cnx, r11 = (Z2 * cny + Y2) * cnx;
+    const int p00 = (Y + Z) & 1, p10 = (Y2 + Z) & 1, p01 = (Y + Z2) & 1, p11 = (Y2 + Z2) & 1;
+    auto C = [&](int row, int par, int a) {
+        const int j = csplit ? ((a + par) & 1) * halfc + ((row + a) >> 1) : row + a;
+        RT_SWEEP_CHECK(j >= 0 && (long long)j < (long long)cnx * cny * cnz);
         return xc[j];
     };
     const T w1 = T(0.75), w2 = T(0.25);
     // y-z weighted columns at coarse x = px - 1, px, px + 1
     auto col = [&](int a) {
-        return w1 * (w1 * C(a, Y, Z) + w2 * C(a, Y2, Z)) + w2 * (w1 * C(a, Y, Z2) + w2 * C(a, Y2, Z2));
+        return w1 * (w1 * C(r00, p00, a) + w2 * C(r10, p10, a)) + w2 * (w1 * C(r01, p01, a) + w2 * C(r11, p11, a));
     };
     const T cm = col(Xm), c0 = col(px), cp = col(Xp);
     v0 = w1 * c0 + w2 * cm;
     v1 = w1 * c0 + w2 * cp;
+}
+
+// b - S x at the two cells of fine pair m = (z ny + y) nx/2 + px of a colour-split level (x, b
+// colour-split; the operator in natural order: diag and the +x/+y/+z face couplings, zero on a
+// non-periodic boundary face): rE for the even-x cell, rO for the odd one.  The even cell has
+// colour (y + z) mod 2; the neighbours of each cell are in the other colour's half.
+template <class T>
+RT_HD void pair_residuals(int nx, int ny, int nz, const int* per, const T* diag, const T* wx, const T* wy,
+                          const T* wz, const T* b, const T* x, int px, int y, int z, T& rE, T& rO) {
+    const int hx = nx >> 1, hxy = hx * ny, half = hxy * nz, plane = nx * ny;
+    const int m = (z * ny + y) * hx + px;
+    const int ce = (y + z) & 1;
+    const T* xe = x + ce * half;         // this row's even cells and the odd cells of the rows above/below
+    const T* xo = x + (1 - ce) * half;   // this row's odd cells and the even cells of the rows above/below
+    const int i = 2 * m;                 // natural index of the even cell
+    RT_SWEEP_CHECK(m >= 0 && m < half);
+    T dE, dO, wE, wO;
+    ld2(diag + i, dE, dO);
+    ld2(wx + i, wE, wO);                 // the face between the two cells, and the odd cell's +x face
+    const T vE = xe[m], vO = xo[m];
+    T sE = wE * vO, sO = wE * vE;
+    if (px > 0) sE += wx[i - 1] * xo[m - 1];
+    else if (per[0]) sE += wx[i - 1 + nx] * xo[m - 1 + hx];
+    if (px + 1 < hx) sO += wO * xe[m + 1];
+    else if (per[0]) sO += wO * xe[m + 1 - hx];
+    // y and z faces: the neighbour pair q, the couplings of the two cells at natural index j, j + 1
+    auto face = [&](const T* w, int j, int q) {
+        RT_SWEEP_CHECK(q >= 0 && q < half && j >= 0 && j + 1 < 2 * half);
+        T w0, w1;
+        ld2(w + j, w0, w1);
+        sE += w0 * xo[q];
+        sO += w1 * xe[q];
+    };
+    if (y + 1 < ny) face(wy, i, m + hx);
+    else if (per[1]) face(wy, i, m + hx - hxy);
+    if (y > 0) face(wy, i - nx, m - hx);
+    else if (per[1]) face(wy, i - nx + plane, m - hx + hxy);
+    if (z + 1 < nz) face(wz, i, m + hxy);
+    else if (per[2]) face(wz, i, m + hxy - half);
+    if (z > 0) face(wz, i - plane, m - hxy);
+    else if (per[2]) face(wz, i - plane + 2 * half, m - hxy + half);
+    rE = b[ce * half + m] - (dE * vE - sE);
+    rO = b[(1 - ce) * half + m] - (dO * vO - sO);
 }
 
 }  // namespace rbp

@@ -156,6 +156,32 @@ long long prolong_pair_host(int nx, int ny, int nz, const int* per, const double
     return g_bad_index;
 }
 
+// out[z][y][x] = b - S x for a colour-split level (x, b given in natural order, permuted here),
+// every fine pair through pair_residuals
+long long resid_host(int nx, int ny, int nz, const int* per, const double* diag, const double* wx, const double* wy,
+                     const double* wz, const double* b, const double* x, double* out) {
+    g_bad_index = 0;
+    const long long n = (long long)nx * ny * nz;
+    std::vector<double> bs(n), xs(n);
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int xx = 0; xx < nx; ++xx) {
+                const long long i = ((long long)z * ny + y) * nx + xx;
+                const long long s = rbp::level_index(1, nx, ny, nz, xx, y, z);
+                bs[s] = b[i];
+                xs[s] = x[i];
+            }
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int px = 0; px < nx / 2; ++px) {
+                double rE, rO;
+                rbp::pair_residuals(nx, ny, nz, per, diag, wx, wy, wz, bs.data(), xs.data(), px, y, z, rE, rO);
+                out[((long long)z * ny + y) * nx + 2 * px] = rE;
+                out[((long long)z * ny + y) * nx + 2 * px + 1] = rO;
+            }
+    return g_bad_index;
+}
+
 // pairs of neighbours (periodic wraps included, a cell that is its own neighbour skipped) that
 // share a colour of the coarse solver's colouring, and the number of colours it uses
 long long colour_conflicts(int nx, int ny, int nz, const int* per, int* ncol_out) {

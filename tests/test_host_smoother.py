@@ -153,3 +153,20 @@ def test_coarse_colouring_has_no_neighbour_conflict(lib, dims, per):
     assert bad == 0
     odd_per = any(p and n % 2 for n, p in zip(dims, per))
     assert ncol.value == (3 if odd_per else 2)
+
+
+@pytest.mark.parametrize("shape,per", [c for c in CASES if c[0][2] % 2 == 0])
+def test_pair_residuals_equal_b_minus_Sx(lib, shape, per):
+    rng = np.random.default_rng(23)
+    diag, *w = _operator(shape, per, rng, np.float64)
+    b = rng.standard_normal(shape)
+    x = rng.standard_normal(shape)
+    nz, ny, nx = shape
+    out = np.zeros(shape)
+    lib.resid_host.restype = ctypes.c_longlong
+    args = [np.ascontiguousarray(a) for a in (diag, *w, b, x)]
+    bad = lib.resid_host(nx, ny, nz, (ctypes.c_int * 3)(*per), *[a.ctypes.data_as(ctypes.c_void_p) for a in args],
+                         out.ctypes.data_as(ctypes.c_void_p))
+    assert bad == 0
+    want = b - (diag * x - _neighbour_sum(w, x))
+    np.testing.assert_allclose(out, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
