@@ -22,7 +22,6 @@
 // The functions are host/device so that a host build can run the passes and compare them with a
 // plain sweep (tests/host/smoother_host.cu).
 #pragma once
-#include <cstdint>
 #include <cuda_runtime.h>
 
 #ifndef RT_HD
@@ -64,59 +63,6 @@ RT_HD void st2(T* p, T a, T b) {
     *reinterpret_cast<typename Vec2<T>::type*>(p) = v;
 }
 
-// Loads of the face arrays with an L2 eviction-priority hint.  The two passes of a sweep read the
-// same six face arrays, the second in reverse plane order, so the planes one pass reads last are
-// the ones the next pass reads first: those loads are marked evict-last (kept in L2 ahead of
-// other lines), the rest evict-first.  A hint changes no value; the host build ignores it.
-RT_HD uint64_t l2_policy(bool keep) {
-#ifdef __CUDA_ARCH__
-    uint64_t p;
-    if (keep)
-        asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    else
-        asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-#else
-    return keep ? 1 : 0;
-#endif
-}
-RT_HD float ldh(const float* p, uint64_t pol) {
-#ifdef __CUDA_ARCH__
-    float v;
-    asm("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
-    return v;
-#else
-    (void)pol;
-    return *p;
-#endif
-}
-RT_HD double ldh(const double* p, uint64_t pol) {
-#ifdef __CUDA_ARCH__
-    double v;
-    asm("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
-    return v;
-#else
-    (void)pol;
-    return *p;
-#endif
-}
-RT_HD void ld2h(const float* p, float& a, float& b, uint64_t pol) {
-#ifdef __CUDA_ARCH__
-    asm("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(a), "=f"(b) : "l"(p), "l"(pol));
-#else
-    (void)pol;
-    ld2(p, a, b);
-#endif
-}
-RT_HD void ld2h(const double* p, double& a, double& b, uint64_t pol) {
-#ifdef __CUDA_ARCH__
-    asm("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(a), "=d"(b) : "l"(p), "l"(pol));
-#else
-    (void)pol;
-    ld2(p, a, b);
-#endif
-}
-
 // launch geometry of a pass: (blocks per row, row blocks, planes)
 RT_HD void pass_grid(int nx, int ny, int nz, int& gx, int& gy, int& gz, int& rows) {
     const int hp = nx / 2;
@@ -148,12 +94,7 @@ struct Pass {
     int rev;        // blocks take the planes from the last to the first
     int quad;       // each thread updates the cells of two pairs (nx a multiple of 4)
     int rows;       // rows per block: kPairs / threads per row (at least 1)
-    int hot0, hot1; // planes [hot0, hot1) are the last the pass reads: face loads kept in L2
 };
-
-// Bytes of face arrays a pass marks evict-last: about a third of the L2, leaving room for the
-// other arrays the passes and the CG stream through it.
-constexpr double kHotFaceBytes = 40e6;
 
 // launch geometry of pass A (threads per row: pairs, or pairs of pairs when A.quad); sets A.rows
 template <class T>
@@ -180,11 +121,6 @@ RT_HD Pass<T> make_pass(int nx, int ny, int nz, const int* per, const T* w6, con
     A.zero = zero;
     A.rev = rev;
     A.quad = nx % 4 == 0;
-    const double plane_bytes = 6.0 * (nx / 2) * (double)ny * sizeof(T);
-    int hot = (int)(kHotFaceBytes / plane_bytes);
-    hot = hot < nz ? hot : nz;
-    A.hot0 = rev ? 0 : nz - hot;
-    A.hot1 = rev ? hot : nz;
     int gx, gy, gz;
     pass_launch(A, gx, gy, gz);
     return A;
@@ -256,12 +192,11 @@ RT_HD T cell_value(const Pass<T>& A, int x, int y, int z) {
     if (!A.zero) {
         int q[6];
         neighbour_pairs(A.nx, A.ny, A.nz, A.per, x, y, z, m, q);
-        const uint64_t pol = l2_policy(z >= A.hot0 && z < A.hot1);
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
             if (q[f] < 0) continue;
             RT_SWEEP_CHECK((long long)q[f] < (long long)A.nx * A.ny * A.nz / 2);
-            const T w = C == 0 ? ldh(A.w[f] + m, pol) : ldh(A.w[f ^ 1] + q[f], pol);
+            const T w = C == 0 ? A.w[f][m] : A.w[f ^ 1][q[f]];
             num += w * A.xo[q[f]];
         }
     }
@@ -280,16 +215,15 @@ RT_HD void quad_values(const Pass<T>& A, int px, int y, int z, T& v0, T& v1) {
     T n0, n1;
     ld2(A.b + m, n0, n1);
     if (!A.zero) {
-        const uint64_t pol = l2_policy(z >= A.hot0 && z < A.hot1);
         // y and z neighbours: pairs q, q + 1 for the two cells
         auto yz = [&](int f, int q) {
             RT_SWEEP_CHECK(q >= 0 && q + 1 < half && (q & 1) == 0);
             T x0, x1, w0, w1;
             ld2(A.xo + q, x0, x1);
             if (C == 0)
-                ld2h(A.w[f] + m, w0, w1, pol);
+                ld2(A.w[f] + m, w0, w1);
             else
-                ld2h(A.w[f ^ 1] + q, w0, w1, pol);
+                ld2(A.w[f ^ 1] + q, w0, w1);
             n0 += w0 * x0;
             n1 += w1 * x1;
         };
@@ -306,8 +240,8 @@ RT_HD void quad_values(const Pass<T>& A, int px, int y, int z, T& v0, T& v1) {
         T xa, xb;
         ld2(A.xo + m, xa, xb);
         T wm0, wm1, wp0, wp1;   // face arrays -x and +x at pairs m, m + 1
-        ld2h(A.w[FXM] + m, wm0, wm1, pol);
-        ld2h(A.w[FXP] + m, wp0, wp1, pol);
+        ld2(A.w[FXM] + m, wm0, wm1);
+        ld2(A.w[FXP] + m, wp0, wp1);
         if (((y + z + C) & 1) == 0) {
             const int qw = px > 0 ? m - 1 : (A.per[0] ? m - 1 + hx : -1);
             if (C == 0) {
@@ -315,7 +249,7 @@ RT_HD void quad_values(const Pass<T>& A, int px, int y, int z, T& v0, T& v1) {
                 n0 += wp0 * xa;
                 n1 += wm1 * xa + wp1 * xb;
             } else {
-                if (qw >= 0) n0 += ldh(A.w[FXP] + qw, pol) * A.xo[qw];
+                if (qw >= 0) n0 += A.w[FXP][qw] * A.xo[qw];
                 n0 += wm0 * xa;
                 n1 += wp0 * xa + wm1 * xb;
             }
@@ -328,7 +262,7 @@ RT_HD void quad_values(const Pass<T>& A, int px, int y, int z, T& v0, T& v1) {
             } else {
                 n0 += wp0 * xa + wm1 * xb;
                 n1 += wp1 * xb;
-                if (qe >= 0) n1 += ldh(A.w[FXM] + qe, pol) * A.xo[qe];
+                if (qe >= 0) n1 += A.w[FXM][qe] * A.xo[qe];
             }
         }
     }
