@@ -28,6 +28,8 @@ What it computes, with the paper passage each module follows:
 * ``helium``     -- the same step for hydrogen + helium gas (Eq. electron_density's helium
   case; species n_HI, n_HeI, n_HeII with the rest by conservation).
 * ``advection``  -- the donor-cell advection pre-step of step (iv) and its transpose.
+* ``multigroup`` -- the step with G radiation groups: Eq. cons_radiation_multifreq integrated
+  over frequency groups with the fixed spectrum kept within each group (Sec. "Physical Model").
 * ``adjoint``    -- the dense discrete adjoint of a multi-step run.
 * ``cosmology``  -- a(t) for the verification cosmologies, the Shapiro-Giroux
   I-front closed form (Eqs. SG-stromgren_radius, SG-solution, SG-tau, SG-F)
