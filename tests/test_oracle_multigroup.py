@@ -148,3 +148,4 @@ def test_complex_step_jacobian_matches_central_differences(iso):
         Jfd[:, j] = (MG.residual(mg, up.reshape(U.shape), bE).ravel() - MG.residual(mg, dn.reshape(U.shape), bE).ravel()) / (2 * h)
     rows = np.abs(Jfd).max(axis=1, keepdims=True) + 1e-300
     assert np.max(np.abs(J - Jfd) / rows) < 1e-5
+
