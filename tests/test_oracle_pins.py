@@ -494,3 +494,82 @@ def test_cosmological_stromgren_front_16cubed():
     r_ode = (3 * Vc / (4 * math.pi)) ** (1 / 3)
     rI = D.ifront_radius(r.nHI, w["rho_b"] / K.M_H, w["dx"], True)
     assert rI == pytest.approx(r_ode, rel=0.12)
+
+
+# ------------------------------------------------ equation of state, diagnostics, local solve
+
+
+def test_temperature_is_the_monatomic_ideal_gas_temperature():
+    """Eqs. eos + temperature with gamma = 5/3: a gas of n_tot = n_H + n_e particles per volume
+    at temperature T holds (3/2) n_tot k T of internal energy per volume; with a bulk velocity
+    the specific total energy adds |v|^2 / 2.  The oracle's temperature of that state is T."""
+    shape = (2, 3, 4)
+    rng = np.random.default_rng(4)
+    rho = 10 ** rng.uniform(-28, -22, shape)
+    nH = rho / K.M_H
+    nHI = nH * rng.uniform(1e-6, 1.0, shape)
+    T = 10 ** rng.uniform(1, 8, shape)
+    v = tuple(rng.normal(0, 3e6, shape) for _ in range(3))
+    n_tot = nH + (nH - nHI)
+    e_h = 1.5 * n_tot * K.K_BOLTZ * T / rho + 0.5 * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2)
+    st = M.Step(nx=4, ny=3, nz=2, dx=1.0, periodic=(True, True, True), rho_b=rho, e_h=e_h, v=v,
+                clump=np.ones(shape), E_n=np.zeros(shape), nHI_n=nHI, a=1.0, adot=0.0, dt=1.0,
+                src_index=np.array([], np.int64), src_ndot=np.array([]), sigma_E=0.0, sigma_G=0.0,
+                eps_src=K.HNU0, isothermal=False)
+    np.testing.assert_allclose(M.temperature(st, np.zeros(shape), nHI), T, rtol=1e-10)
+
+
+def test_ifront_radius_of_a_resolved_sphere():
+    """An octant holding a sphere of radius R about the corner, each cell ionised in proportion
+    to the part of its volume inside the sphere (from 8^3 sub-cell samples): the equivalent-volume
+    radius is R to the sampling error, and with whole-cell ionisation (cell centres inside) the
+    error falls as the grid is refined."""
+    R = 0.62
+    for n in (16, 32):
+        dx = 1.0 / n
+        s = (np.arange(8) + 0.5) / 8.0
+        z, y, x = np.indices((n, n, n))
+        frac = np.zeros((n, n, n))
+        for a in s:
+            for b in s:
+                for c in s:
+                    frac += (((x + a) * dx) ** 2 + ((y + b) * dx) ** 2 + ((z + c) * dx) ** 2 <= R * R)
+        frac /= 512.0
+        nH = np.ones((n, n, n))
+        rI = D.ifront_radius(nH * (1.0 - frac), nH, dx, True)
+        assert rI == pytest.approx(R, rel=2e-3)
+    errs = []
+    for n in (16, 32, 64):
+        dx = 1.0 / n
+        z, y, x = np.indices((n, n, n))
+        inside = (((x + 0.5) * dx) ** 2 + ((y + 0.5) * dx) ** 2 + ((z + 0.5) * dx) ** 2 <= R * R)
+        nH = np.ones((n, n, n))
+        errs.append(abs(D.ifront_radius(nH * (1.0 - inside), nH, dx, True) / R - 1.0))
+    assert errs[2] < errs[0] and errs[2] < 0.01
+
+
+def test_local_solve_matches_an_independent_root_finder():
+    """The oracle's cell-local solution (damped 2x2 Newton) against SciPy's hybrid Powell method
+    on the same local equations, started from the step's starting state, on sampled cells of a
+    non-isothermal state: both find the same root."""
+    from scipy import optimize
+    st = _smooth_state((5, 4, 3), 12, isothermal=False)
+    U = N.initial_iterate(st)
+    U[2] = 2.0 * st.E_n
+    Uo = N.local_solve(st, U)
+    rng = np.random.default_rng(0)
+    cells = rng.choice(st.N, 12, replace=False)
+    se = np.maximum(M.internal_energy_h(st), M.E_FLOOR_INT())
+    for c in cells:
+        k = np.unravel_index(c, st.shape)
+
+        def f(v):
+            ec = np.full(st.shape, Uo[0][k]); n = np.full(st.shape, Uo[1][k])
+            ec[k], n[k] = v[0] * se[k], v[1] * st.n_H[k]
+            fe, fn = M.local_residual(st, ec, n, U[2])
+            return [np.real(fe[k]) / se[k], np.real(fn[k]) / st.n_H[k]]
+
+        sol = optimize.root(f, [0.0, st.nHI_n[k] / st.n_H[k]], method="hybr", tol=1e-14)
+        assert sol.success
+        assert sol.x[0] * se[k] == pytest.approx(Uo[0][k], rel=1e-8, abs=1e-10 * se[k])
+        assert sol.x[1] * st.n_H[k] == pytest.approx(Uo[1][k], rel=1e-8, abs=1e-12 * st.n_H[k])
